@@ -1,0 +1,161 @@
+/*
+ * aaomg.h -- C ABI of the GB300 (sm_103a) all-at-once multigrid library for
+ * the discretised Poisson control problem.
+ *
+ * The method (Takacs, "Efficient smoothers for all-at-once multigrid methods
+ * for Poisson and Stokes control problems"):
+ *
+ *   minimise 1/2 ||y - y_D||^2 + alpha/2 ||u||^2  subject to  -Lap y + y = u,
+ *   dy/dn = 0 on the boundary of the unit square            (section 1)
+ *
+ * discretised with Courant (P1) elements on the uniform triangulation with
+ * h = 2^-levels whose cells are split by their SW-NE diagonal, gives the
+ * saddle-point system of eq. (mp2)
+ *
+ *   A x = f,  A = [[M, K], [K, -alpha^{-1} M]],  x = (y, lambda),  f = (M y_D, 0),
+ *
+ * with M the mass matrix and K the matrix of (grad y, grad v) + (y, v); the
+ * control is u = lambda / alpha.  The library solves it with the multigrid
+ * iteration of section 2 (smoothing, defect restriction by the transpose of
+ * the canonical embedding, recursive coarse correction, prolongation,
+ * post-smoothing; exact solve on the coarsest grid h = 1/2), with the
+ * normal-equation smoother (Algorithm 1), the least-squares Gauss-Seidel
+ * smoother LSGS (Algorithm 2) or its symmetric form sLSGS.
+ *
+ * Vectors.  A grid level with n = 2^k cells per side has N = (n+1)^2 nodes;
+ * node (i h, j h), 0 <= i, j <= n, has index j*(n+1) + i.  Every vector passed
+ * to this library is a contiguous array of 2N doubles: the y (or first) field
+ * in elements [0, N), the lambda (or second) field in [N, 2N).
+ *
+ * Memory.  Functions whose vector arguments are documented as device pointers
+ * take CUDA device (or managed) memory on the current device, owned by the
+ * caller; the library never frees them and keeps no reference after the call
+ * returns.  The library owns its handle and the workspaces it allocates in
+ * mg_setup; mg_destroy frees them.  A `stream` argument is a cudaStream_t
+ * passed as void* (NULL = the legacy default stream); all device work of a call
+ * is ordered on that stream, and calls that return scalars (iteration counts,
+ * residual norms) synchronise with it before returning.
+ *
+ * Errors.  Every int-returning function returns AAOMG_OK (0) or a negative
+ * AAOMG_ERR_* code; mg_strerror() names it and mg_last_error() gives the
+ * message of the calling thread's last failure.  No C++ exception crosses this
+ * interface.  A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef AAOMG_H
+#define AAOMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define AAOMG_API __attribute__((visibility("default")))
+#else
+#define AAOMG_API
+#endif
+
+#define AAOMG_OK 0
+#define AAOMG_ERR_BAD_ARG (-1)       /* invalid argument: null pointer, level or alpha out of range */
+#define AAOMG_ERR_OOM (-2)           /* device or host allocation failed */
+#define AAOMG_ERR_CUDA (-3)          /* a CUDA runtime call failed (message in mg_last_error) */
+#define AAOMG_ERR_NOT_CONVERGED (-4) /* max_iter reached above tol; x holds the last iterate */
+#define AAOMG_ERR_DIVERGED (-5)      /* residual became NaN/Inf or grew by more than 1e6 */
+#define AAOMG_ERR_NO_DEVICE (-7)     /* no CUDA device, or it is not sm_103 */
+
+#define AAOMG_MAX_LEVELS 13
+
+/* smoother (section 2) */
+#define MG_SMOOTHER_NE 0    /* normal equation smoother, Algorithm 1, damped by tau */
+#define MG_SMOOTHER_LSGS 1  /* least-squares Gauss-Seidel, Algorithm 2, undamped */
+#define MG_SMOOTHER_SLSGS 2 /* symmetric LSGS: LSGS step then LSGS step in reversed order */
+
+/* precision */
+#define MG_PREC_FP64 0        /* every operation in FP64 */
+#define MG_PREC_FP32_REFINE 1 /* FP32 multigrid cycles inside FP64 iterative refinement */
+
+typedef struct mg_ctx* mg_handle;
+
+/* Options; an all-zero struct selects every default. */
+typedef struct mg_options {
+    int smoother;     /* MG_SMOOTHER_*; default NE (0) */
+    int nu_pre;       /* pre-smoothing steps;  <= 0: 2 (sLSGS: 1) */
+    int nu_post;      /* post-smoothing steps; <= 0: 2 (sLSGS: 1) */
+    int cycle;        /* coarse-grid steps per level: 1 V-cycle, 2 W-cycle; 0: W */
+    int precision;    /* MG_PREC_*; default FP64 */
+    double tau;       /* NE damping; <= 0: 0.4 (the paper's value for Poisson control) */
+    int k_variant;    /* 0: K = stiffness + mass (default); 1: K = bare stiffness matrix */
+    int max_iter;     /* mg_solve iteration cap; <= 0: 100 */
+    int inner_cycles; /* FP32_REFINE: FP32 cycles per refinement step; <= 0: 3 */
+    int coarse_level; /* levels <= this run inside one single-block kernel; < 0: default, 0: none */
+} mg_options;
+
+/* Build the hierarchy for h = 2^-levels (1 <= levels <= 13; level 1 is the
+ * coarsest grid h = 1/2 with 18 unknowns) and regularisation alpha > 0
+ * (finite).  Allocates all device workspaces on the current device.  On
+ * success *out is a new handle.  Errors: BAD_ARG, NO_DEVICE, OOM, CUDA. */
+AAOMG_API int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out);
+
+/* Free a handle and its workspaces (NULL is ignored).  Synchronises the device. */
+AAOMG_API void mg_destroy(mg_handle h);
+
+/* Number of nodes N per field on the finest level ((2^levels+1)^2). */
+AAOMG_API long long mg_num_nodes(mg_handle h);
+
+/* f = (M y_D, 0), eq. (mp2): yD (N doubles) and f (2N doubles) are device
+ * pointers. */
+AAOMG_API int mg_rhs_from_yd(mg_handle h, const double* yD, double* f, void* stream);
+
+/* r = f - A x on the finest level (device pointers, 2N doubles each; r may be
+ * NULL).  If relres is non-NULL it receives ||r||_{L^-1} / ||f||_{L^-1}, with
+ * ||v||_{L^-1}^2 = v^T L^{-1} v and L = diag(Q) of section 2 (synchronises). */
+AAOMG_API int mg_residual(mg_handle h, const double* f, const double* x, double* r, double* relres, void* stream);
+
+/* `steps` smoothing steps of the configured smoother on the finest level:
+ * x <- x + Ahat^{-1}(f - A x) (section 2; Algorithm 1 / Algorithm 2), in place
+ * on x.  In FP32_REFINE mode the steps run in FP32 on x and f rounded to
+ * single precision.  Device pointers, 2N doubles each. */
+AAOMG_API int mg_smooth(mg_handle h, const double* f, double* x, int steps, void* stream);
+
+/* Defect restriction of section 2 on the finest level:
+ * fc = I_k^{k-1} (f - A x), with I_k^{k-1} the transpose of the canonical
+ * embedding.  f, x: 2N doubles; fc: 2Nc doubles for the next coarser level.
+ * Requires levels >= 2.  Device pointers. */
+AAOMG_API int mg_restrict(mg_handle h, const double* f, const double* x, double* fc, void* stream);
+
+/* Prolongation and correction of section 2: x += I_{k-1}^k xc (canonical
+ * embedding of the coarse P1 space).  xc: 2Nc doubles, x: 2N doubles.
+ * Requires levels >= 2.  Device pointers. */
+AAOMG_API int mg_prolong_add(mg_handle h, const double* xc, double* x, void* stream);
+
+/* One multigrid iteration (section 2) on the finest level, in place on x.
+ * FP64 mode: one cycle.  FP32_REFINE mode: one refinement step (FP64 defect,
+ * `inner_cycles` FP32 cycles on it from zero, FP64 update).  Device pointers. */
+AAOMG_API int mg_cycle(mg_handle h, const double* f, double* x, void* stream);
+
+/* Iterate from the initial guess in x until ||f - A x||_{L^-1} <= tol *
+ * ||f||_{L^-1} or max_iter iterations.  *iters (may be NULL) gets the number
+ * of iterations, *relres (may be NULL) the final relative residual.  Returns
+ * NOT_CONVERGED if the cap was hit (x holds the last iterate), DIVERGED on
+ * NaN or blow-up.  Device pointers. */
+AAOMG_API int mg_solve(mg_handle h, const double* f, double* x, double tol, int* iters, double* relres, void* stream);
+
+/* mg_solve with f and x in HOST memory (pinned or pageable): copies f and x to
+ * the device, solves, and copies x back, all on `stream`. */
+AAOMG_API int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol, int* iters, double* relres,
+                  void* stream);
+
+/* Relative residual after each iteration of the last mg_solve: buf[0] is the
+ * initial one; *n receives the count written (<= cap). */
+AAOMG_API int mg_get_history(mg_handle h, double* buf, int cap, int* n);
+
+/* Kernel launches issued by this handle since it was created (for reports). */
+AAOMG_API long long mg_kernel_launches(mg_handle h);
+
+/* Name of an AAOMG_* code; message of the calling thread's last failure. */
+AAOMG_API const char* mg_strerror(int code);
+AAOMG_API const char* mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAOMG_H */

@@ -1,0 +1,219 @@
+"""ctypes binding of the C ABI in ``include/aaomg.h`` (``libaaomg.so``).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Vectors are torch float64 CUDA tensors (device calls) or numpy float64 arrays
+(``solve_host``); the current torch CUDA stream is passed to every call.  If the
+library is missing or no sm_103 GPU is present the calls raise -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libaaomg.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "aaomg.h")
+
+SMOOTHER = {"ne": 0, "lsgs": 1, "slsgs": 2}
+PRECISION = {"fp64": 0, "fp32_refine": 1}
+CYCLE = {"V": 1, "W": 2}
+
+OK, ERR_BAD_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_NO_DEVICE = 0, -1, -2, -3, -4, -5, -7
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MGError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("smoother", ctypes.c_int),
+        ("nu_pre", ctypes.c_int),
+        ("nu_post", ctypes.c_int),
+        ("cycle", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("k_variant", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("inner_cycles", ctypes.c_int),
+        ("coarse_level", ctypes.c_int),
+    ]
+
+
+def header_functions() -> list[str]:
+    """Names of the functions the C header declares."""
+    text = open(HEADER).read()
+    return re.findall(r"AAOMG_API\s+[\w\s\*]+?\b(mg_\w+)\s*\(", text)
+
+
+def load():
+    """Load libaaomg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        H = ctypes.c_void_p
+        I, D, P = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        pI, pD = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "mg_setup": (I, [I, D, ctypes.POINTER(Options), ctypes.POINTER(H)]),
+            "mg_destroy": (None, [H]),
+            "mg_num_nodes": (ctypes.c_longlong, [H]),
+            "mg_rhs_from_yd": (I, [H, P, P, P]),
+            "mg_residual": (I, [H, P, P, P, pD, P]),
+            "mg_smooth": (I, [H, P, P, I, P]),
+            "mg_restrict": (I, [H, P, P, P, P]),
+            "mg_prolong_add": (I, [H, P, P, P]),
+            "mg_cycle": (I, [H, P, P, P]),
+            "mg_solve": (I, [H, P, P, D, pI, pD, P]),
+            "mg_solve_host": (I, [H, P, P, D, pI, pD, P]),
+            "mg_get_history": (I, [H, pD, I, pI]),
+            "mg_kernel_launches": (ctypes.c_longlong, [H]),
+            "mg_strerror": (ctypes.c_char_p, [I]),
+            "mg_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(code: int, where: str, allow=()):
+    if code != OK and code not in allow:
+        lib = load()
+        raise MGError(code, where, lib.mg_last_error().decode() or lib.mg_strerror(code).decode())
+    return code
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, n=None):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One multigrid hierarchy (levels 1..L) for one alpha, owned by the library."""
+
+    def __init__(self, levels: int, alpha: float, smoother: str = "lsgs", precision: str = "fp64",
+                 cycle: str = "W", nu_pre: int = 0, nu_post: int = 0, tau: float = 0.0, k_variant: int = 0,
+                 max_iter: int = 0, inner_cycles: int = 0, coarse_level: int = -1):
+        self._lib = load()
+        self.levels, self.alpha = int(levels), float(alpha)
+        self.smoother, self.precision, self.cycle_kind = smoother, precision, cycle
+        opt = Options(SMOOTHER[smoother], int(nu_pre), int(nu_post), CYCLE[cycle], PRECISION[precision],
+                      float(tau), int(k_variant), int(max_iter), int(inner_cycles), int(coarse_level))
+        h = ctypes.c_void_p()
+        _check(self._lib.mg_setup(self.levels, self.alpha, ctypes.byref(opt), ctypes.byref(h)), "mg_setup")
+        self._h = h
+        self.N = int(self._lib.mg_num_nodes(h))
+        self.nc = ((1 << (self.levels - 1)) + 1) ** 2 if self.levels > 1 else 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- device calls ------------------------------------------------------
+    def rhs_from_yd(self, yD, f=None):
+        import torch
+
+        f = torch.empty(2 * self.N, dtype=torch.float64, device=yD.device) if f is None else f
+        _check(self._lib.mg_rhs_from_yd(self._h, _dptr(yD, self.N), _dptr(f, 2 * self.N), _stream()), "mg_rhs_from_yd")
+        return f
+
+    def residual(self, f, x, r=None):
+        rr = ctypes.c_double()
+        rp = _dptr(r, 2 * self.N) if r is not None else None
+        _check(self._lib.mg_residual(self._h, _dptr(f, 2 * self.N), _dptr(x, 2 * self.N), rp, ctypes.byref(rr),
+                                     _stream()), "mg_residual")
+        return rr.value
+
+    def smooth(self, f, x, steps: int = 1):
+        _check(self._lib.mg_smooth(self._h, _dptr(f, 2 * self.N), _dptr(x, 2 * self.N), int(steps), _stream()),
+               "mg_smooth")
+        return x
+
+    def restrict(self, f, x, fc=None):
+        import torch
+
+        fc = torch.empty(2 * self.nc, dtype=torch.float64, device=f.device) if fc is None else fc
+        _check(self._lib.mg_restrict(self._h, _dptr(f, 2 * self.N), _dptr(x, 2 * self.N), _dptr(fc, 2 * self.nc),
+                                     _stream()), "mg_restrict")
+        return fc
+
+    def prolong_add(self, xc, x):
+        _check(self._lib.mg_prolong_add(self._h, _dptr(xc, 2 * self.nc), _dptr(x, 2 * self.N), _stream()),
+               "mg_prolong_add")
+        return x
+
+    def cycle(self, f, x):
+        _check(self._lib.mg_cycle(self._h, _dptr(f, 2 * self.N), _dptr(x, 2 * self.N), _stream()), "mg_cycle")
+        return x
+
+    def solve(self, f, x, tol: float = 1e-8, raise_on_fail: bool = True):
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        code = self._lib.mg_solve(self._h, _dptr(f, 2 * self.N), _dptr(x, 2 * self.N), float(tol), ctypes.byref(it),
+                                  ctypes.byref(rr), _stream())
+        if raise_on_fail:
+            _check(code, "mg_solve")
+        return it.value, rr.value, code
+
+    def solve_host(self, f, x, tol: float = 1e-8, raise_on_fail: bool = True):
+        """f, x: C-contiguous float64 numpy arrays (x in/out) in host memory."""
+        import numpy as np
+
+        for a in (f, x):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == 2 * self.N):
+                raise TypeError("expected contiguous float64 numpy arrays of 2N elements")
+        if not x.flags.writeable:
+            raise ValueError("x must be writeable")
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        code = self._lib.mg_solve_host(self._h, ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(x.ctypes.data),
+                                       float(tol), ctypes.byref(it), ctypes.byref(rr), _stream())
+        if raise_on_fail:
+            _check(code, "mg_solve_host")
+        return it.value, rr.value, code
+
+    def history(self):
+        buf = (ctypes.c_double * 1024)()
+        n = ctypes.c_int()
+        _check(self._lib.mg_get_history(self._h, buf, 1024, ctypes.byref(n)), "mg_get_history")
+        return [buf[i] for i in range(n.value)]
+
+    def launches(self) -> int:
+        return int(self._lib.mg_kernel_launches(self._h))

@@ -1,0 +1,644 @@
+// aaomg.cu -- host side of the library: the handle, the grid hierarchy, the
+// multigrid cycle of section 2 issued as kernel launches (recorded once into a
+// CUDA graph), the solve loop with FP64 iterative refinement, and the C ABI
+// declared in include/aaomg.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "aaomg.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace aaomg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(AAOMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Lev {
+    int n = 0, ld = 0;
+    int64_t fs = 0;
+    void* x = nullptr;
+    void* f = nullptr;
+    void* rh = nullptr;
+    LevelP<float> pf{};
+    LevelP<double> pd{};
+};
+
+template <typename T>
+const LevelP<T>& lp(const Lev& v);
+template <>
+const LevelP<float>& lp<float>(const Lev& v) {
+    return v.pf;
+}
+template <>
+const LevelP<double>& lp<double>(const Lev& v) {
+    return v.pd;
+}
+
+// Coefficients of one level in the parametrised form A = [[M, cK], [cK, -dM]],
+// L_y = diag(M + beta K), L_lambda = d L_y (see common.cuh), computed in FP64.
+template <typename T>
+LevelP<T> make_params(int n, int ld, int64_t fs, double alpha, bool scaled, double km, double tau) {
+    LevelP<T> P{};
+    P.n = n;
+    P.ld = ld;
+    P.fs = fs;
+    const double h = 1.0 / n, h2 = h * h, beta = std::sqrt(alpha);
+    const double c = scaled ? beta : 1.0, d = scaled ? 1.0 : 1.0 / alpha;
+    P.h2 = (T)h2;
+    P.c = (T)c;
+    P.d = (T)d;
+    P.invd = (T)(1.0 / d);
+    P.beta = (T)beta;
+    P.km = (T)km;
+    P.tau = (T)tau;
+    auto Ly = [&](int i, int j) {
+        double m[7], k[7];
+        row_coeffs_general<double>(i, j, n, h2, km, m, k);
+        return m[0] + beta * k[0];
+    };
+    auto Nd = [&](int i, int j, int field) {
+        double m[7], k[7], s = 0.0;
+        row_coeffs_general<double>(i, j, n, h2, km, m, k);
+        for (int o = 0; o < 7; ++o) {
+            int ii = i + DI(o), jj = j + DJ(o);
+            if (!in_grid(ii, jj, n)) continue;
+            double num = field == 0 ? m[o] * m[o] + c * c * k[o] * k[o] / d : c * c * k[o] * k[o] + d * m[o] * m[o];
+            s += num / Ly(ii, jj);
+        }
+        return s;
+    };
+    {
+        double m[7], k[7];
+        row_coeffs_general<double>(1, 1, n, h2, km, m, k);
+        P.mC = (T)m[0];
+        P.mO = (T)m[1];
+        P.kC = (T)k[0];
+        P.kE = (T)k[1];
+        P.kD = (T)k[5];
+        P.invLy_int = (T)(1.0 / Ly(1, 1));
+    }
+    const int rep3[3] = {0, 1, n};
+    for (int cy = 0; cy < 3; ++cy)
+        for (int cx = 0; cx < 3; ++cx) P.invLy[cx + 3 * cy] = (T)(1.0 / Ly(rep3[cx], rep3[cy]));
+    if (n >= 4) {
+        const int rep5[5] = {0, 1, 2, n - 1, n};
+        for (int cy = 0; cy < 5; ++cy)
+            for (int cx = 0; cx < 5; ++cx) {
+                P.invNy[cx + 5 * cy] = (T)(1.0 / Nd(rep5[cx], rep5[cy], 0));
+                P.invNl[cx + 5 * cy] = (T)(1.0 / Nd(rep5[cx], rep5[cy], 1));
+            }
+        P.invNy_int = (T)(1.0 / Nd(2, 2, 0));
+        P.invNl_int = (T)(1.0 / Nd(2, 2, 1));
+    }
+    return P;
+}
+
+// Dense inverse of the coarsest operator (n = 2, 18 unknowns) by Gauss-Jordan
+// elimination with partial pivoting, in FP64.
+bool coarse_inverse(double alpha, bool scaled, double km, double* inv) {
+    const int n = 2, nn = 9, m = 18;
+    const double h2 = 0.25, beta = std::sqrt(alpha);
+    const double c = scaled ? beta : 1.0, d = scaled ? 1.0 : 1.0 / alpha;
+    double a[18][36];
+    std::memset(a, 0, sizeof(a));
+    for (int j = 0; j <= n; ++j)
+        for (int i = 0; i <= n; ++i) {
+            double mm[7], kk[7];
+            row_coeffs_general<double>(i, j, n, h2, km, mm, kk);
+            int p = j * 3 + i;
+            for (int o = 0; o < 7; ++o) {
+                int ii = i + DI(o), jj = j + DJ(o);
+                if (!in_grid(ii, jj, n)) continue;
+                int q = jj * 3 + ii;
+                a[p][q] += mm[o];
+                a[p][nn + q] += c * kk[o];
+                a[nn + p][q] += c * kk[o];
+                a[nn + p][nn + q] += -d * mm[o];
+            }
+        }
+    for (int i = 0; i < m; ++i) a[i][m + i] = 1.0;
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+        if (a[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int t = 0; t < 2 * m; ++t) std::swap(a[piv][t], a[col][t]);
+        double s = 1.0 / a[col][col];
+        for (int t = 0; t < 2 * m; ++t) a[col][t] *= s;
+        for (int r = 0; r < m; ++r)
+            if (r != col && a[r][col] != 0.0) {
+                double fct = a[r][col];
+                for (int t = 0; t < 2 * m; ++t) a[r][t] -= fct * a[col][t];
+            }
+    }
+    for (int r = 0; r < m; ++r)
+        for (int t = 0; t < m; ++t) inv[r * m + t] = a[r][m + t];
+    return true;
+}
+
+}  // namespace
+
+struct mg_ctx {
+    int L = 0;
+    double alpha = 0.0, beta = 0.0;
+    mg_options o{};
+    int dev = 0;
+    bool fp32 = false;
+    Lev lev[AAOMG_MAX_LEVELS + 1];
+    LevelP<double> fine64{};  // the paper's system on the finest level, user layout
+    double* x64 = nullptr;    // FP64 finest iterate and right-hand side (internal copies)
+    double* f64 = nullptr;
+    double* ainv = nullptr;   // coarsest inverse in the cycle's scaling
+    double* part = nullptr;   // per-block partial sums
+    double* red = nullptr;    // reduced norms (device)
+    double* h_red = nullptr;  // pinned host copy
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;
+    long long launches = 0;
+    long long rec_kernels = 0;
+    std::vector<double> hist;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int dalloc(mg_ctx* H, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? AAOMG_ERR_OOM : AAOMG_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    H->allocs.push_back(*p);
+    return AAOMG_OK;
+}
+
+// ------------------------------------------------------------ the cycle --
+
+template <typename T>
+void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
+    if (steps <= 0) return;
+    Lev& v = H->lev[l];
+    const LevelP<T>& P = lp<T>(v);
+    T* x = (T*)v.x;
+    T* f = (T*)v.f;
+    T* rh = (T*)v.rh;
+    switch (H->o.smoother) {
+    case MG_SMOOTHER_NE:
+        for (int m = 0; m < steps; ++m) {
+            launch_resid_hat<T>(P, f, x, rh, s);
+            launch_ne_update<T>(P, x, rh, s);
+            H->rec_kernels += 2;
+        }
+        break;
+    default: {
+        launch_resid_hat<T>(P, f, x, rh, s);
+        H->rec_kernels += 1;
+        for (int m = 0; m < steps; ++m) {
+            for (int field = 0; field < 2; ++field)
+                for (int c = 0; c < 7; ++c) launch_lsgs_phase<T>(P, field, kColourSeq[c], x, rh, s);
+            H->rec_kernels += 14;
+            if (H->o.smoother == MG_SMOOTHER_SLSGS) {
+                for (int field = 1; field >= 0; --field)
+                    for (int c = 6; c >= 0; --c) launch_lsgs_phase<T>(P, field, kColourSeq[c], x, rh, s);
+                H->rec_kernels += 14;
+            }
+        }
+    }
+    }
+}
+
+template <typename T>
+void cycle(mg_ctx* H, int l, cudaStream_t s) {
+    Lev& v = H->lev[l];
+    const LevelP<T>& P = lp<T>(v);
+    if (l == 1) {
+        launch_coarsest<T>(H->ainv, (const T*)v.f, (T*)v.x, P.fs, s);
+        H->rec_kernels += 1;
+        return;
+    }
+    Lev& c = H->lev[l - 1];
+    smooth<T>(H, l, H->o.nu_pre, s);
+    launch_restrict<T>(P, lp<T>(c), (const T*)v.f, (const T*)v.x, (T*)c.f, (T*)c.x, s);
+    H->rec_kernels += 1;
+    for (int g = 0; g < H->o.cycle; ++g) cycle<T>(H, l - 1, s);
+    launch_prolong<T>(P, lp<T>(c), (const T*)c.x, (T*)v.x, s);
+    H->rec_kernels += 1;
+    smooth<T>(H, l, H->o.nu_post, s);
+}
+
+// One iteration body (without the residual/norm launch):
+//   FP64:        one cycle on lev[L] (x, f internal FP64 copies)
+//   FP32_REFINE: x~ = 0; inner_cycles FP32 cycles on (lev[L].f = scaled defect);
+//                x64 += S^{-1} x~
+int record_iteration(mg_ctx* H, cudaStream_t s) {
+    Lev& v = H->lev[H->L];
+    if (!H->fp32) {
+        cycle<double>(H, H->L, s);
+    } else {
+        CK(cudaMemsetAsync(v.x, 0, sizeof(float) * 2 * v.fs, s));
+        for (int c = 0; c < H->o.inner_cycles; ++c) cycle<float>(H, H->L, s);
+        launch_refine_update(H->fine64, H->x64, (const float*)v.x, v.ld, v.fs, s);
+        H->rec_kernels += 1;
+    }
+    return AAOMG_OK;
+}
+
+int build_graph(mg_ctx* H) {
+    CK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal));
+    H->rec_kernels = 0;
+    int rc = record_iteration(H, H->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(H->cap, &g);
+    if (rc != AAOMG_OK) return rc;
+    if (e != cudaSuccess) return fail(AAOMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    H->graph = g;
+    CK(cudaGraphInstantiate(&H->gexec, g, 0));
+    H->graph_kernels = H->rec_kernels;
+    return AAOMG_OK;
+}
+
+double* iter_x(mg_ctx* H) { return H->fp32 ? H->x64 : (double*)H->lev[H->L].x; }
+double* iter_f(mg_ctx* H) { return H->fp32 ? H->f64 : (double*)H->lev[H->L].f; }
+
+// residual of the FP64 iterate; in FP32 mode also writes the scaled FP32 defect
+// into the inner finest right-hand side.  Leaves norms in H->h_red after sync.
+int residual_norms(mg_ctx* H, cudaStream_t s, bool write_inner) {
+    Lev& v = H->lev[H->L];
+    float* fin = (H->fp32 && write_inner) ? (float*)v.f : nullptr;
+    launch_resid64(H->fine64, iter_f(H), iter_x(H), nullptr, fin, v.ld, v.fs, H->part, kResidBlocks, H->red, s);
+    H->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(H->h_red, H->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AAOMG_OK;
+}
+
+int run_iteration(mg_ctx* H, cudaStream_t s) {
+    CK(cudaGraphLaunch(H->gexec, s));
+    H->launches += H->graph_kernels;
+    return AAOMG_OK;
+}
+
+int check_handle(mg_handle h) {
+    if (!h) return fail(AAOMG_ERR_BAD_ARG, "null handle");
+    cudaError_t e = cudaSetDevice(h->dev);
+    if (e != cudaSuccess) return fail(AAOMG_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return AAOMG_OK;
+}
+
+int64_t vec_bytes(mg_ctx* H) { return (int64_t)2 * H->fine64.fs * (int64_t)sizeof(double); }
+
+// solve loop on the internal FP64 copies
+int solve_internal(mg_ctx* H, double tol, int* iters, double* relres, cudaStream_t s) {
+    H->hist.clear();
+    int it = 0;
+    double rr = 0.0, r0 = 0.0;
+    int status = AAOMG_OK;
+    for (;;) {
+        int rc = residual_norms(H, s, true);
+        if (rc) return rc;
+        double fn = H->h_red[1] > 0.0 ? H->h_red[1] : 1.0;
+        rr = std::sqrt(H->h_red[0] / fn);
+        H->hist.push_back(rr);
+        if (it == 0) r0 = rr;
+        if (!std::isfinite(rr) || rr > 1e6 * (r0 > 0 ? r0 : 1.0)) {
+            status = fail(AAOMG_ERR_DIVERGED, "residual diverged");
+            break;
+        }
+        if (rr <= tol) break;
+        if (it >= H->o.max_iter) {
+            status = fail(AAOMG_ERR_NOT_CONVERGED, "max_iter reached");
+            break;
+        }
+        rc = run_iteration(H, s);
+        if (rc) return rc;
+        ++it;
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return status;
+}
+
+// copy the caller's (FP64, paper's scaling) vector into the FP32 finest level
+void to_inner(mg_ctx* H, const double* v, void* out, double s_l, cudaStream_t s) {
+    Lev& w = H->lev[H->L];
+    launch_to_f32(w.n, v, H->fine64.ld, H->fine64.fs, (float*)out, w.ld, w.fs, s_l, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI --
+extern "C" {
+
+const char* mg_strerror(int code) {
+    switch (code) {
+    case AAOMG_OK: return "ok";
+    case AAOMG_ERR_BAD_ARG: return "bad argument";
+    case AAOMG_ERR_OOM: return "out of memory";
+    case AAOMG_ERR_CUDA: return "CUDA error";
+    case AAOMG_ERR_NOT_CONVERGED: return "not converged";
+    case AAOMG_ERR_DIVERGED: return "diverged";
+    case AAOMG_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    default: return "unknown error";
+    }
+}
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+void mg_destroy(mg_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->dev);
+    cudaDeviceSynchronize();
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_red) cudaFreeHost(h->h_red);
+    delete h;
+}
+
+int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
+    if (!out) return fail(AAOMG_ERR_BAD_ARG, "out is null");
+    *out = nullptr;
+    if (levels < 1 || levels > AAOMG_MAX_LEVELS) return fail(AAOMG_ERR_BAD_ARG, "levels must be in [1, 13]");
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(AAOMG_ERR_BAD_ARG, "alpha must be positive and finite");
+    mg_options o{};
+    if (opt) o = *opt;
+    if (o.smoother < 0 || o.smoother > MG_SMOOTHER_SLSGS) return fail(AAOMG_ERR_BAD_ARG, "unknown smoother");
+    if (o.precision < 0 || o.precision > MG_PREC_FP32_REFINE) return fail(AAOMG_ERR_BAD_ARG, "unknown precision");
+    if (o.cycle < 0 || o.cycle > 2) return fail(AAOMG_ERR_BAD_ARG, "cycle must be 1 (V) or 2 (W)");
+    if (o.k_variant < 0 || o.k_variant > 1) return fail(AAOMG_ERR_BAD_ARG, "k_variant must be 0 or 1");
+    const int dflt_nu = o.smoother == MG_SMOOTHER_SLSGS ? 1 : 2;
+    if (o.nu_pre <= 0) o.nu_pre = dflt_nu;
+    if (o.nu_post <= 0) o.nu_post = dflt_nu;
+    if (o.cycle == 0) o.cycle = 2;
+    if (!(o.tau > 0.0)) o.tau = 0.4;
+    if (o.max_iter <= 0) o.max_iter = 100;
+    if (o.inner_cycles <= 0) o.inner_cycles = 3;
+
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(AAOMG_ERR_NO_DEVICE, "no CUDA device");
+    CK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(AAOMG_ERR_NO_DEVICE, std::string("device is not sm_103: ") + prop.name);
+
+    mg_ctx* H = new (std::nothrow) mg_ctx();
+    if (!H) return fail(AAOMG_ERR_OOM, "host allocation");
+    H->L = levels;
+    H->alpha = alpha;
+    H->beta = std::sqrt(alpha);
+    H->o = o;
+    H->dev = dev;
+    H->fp32 = o.precision == MG_PREC_FP32_REFINE;
+    const double km = o.k_variant == 0 ? 1.0 : 0.0;
+    int rc = AAOMG_OK;
+    {
+        int n = 1 << levels;
+        H->fine64 = make_params<double>(n, n + 1, (int64_t)(n + 1) * (n + 1), alpha, false, km, o.tau);
+    }
+    for (int l = 1; l <= levels; ++l) {
+        Lev& v = H->lev[l];
+        v.n = 1 << l;
+        v.ld = v.n + 1;
+        v.fs = (int64_t)v.ld * (v.n + 1);
+        size_t es = H->fp32 ? sizeof(float) : sizeof(double);
+        size_t bytes = es * 2 * (size_t)v.fs;
+        if ((rc = dalloc(H, &v.x, bytes)) || (rc = dalloc(H, &v.f, bytes)) || (rc = dalloc(H, &v.rh, bytes))) break;
+        CK(cudaMemset(v.x, 0, bytes));
+        CK(cudaMemset(v.f, 0, bytes));
+        CK(cudaMemset(v.rh, 0, bytes));
+        v.pd = make_params<double>(v.n, v.ld, v.fs, alpha, false, km, o.tau);
+        v.pf = make_params<float>(v.n, v.ld, v.fs, alpha, true, km, o.tau);
+    }
+    if (rc) {
+        mg_destroy(H);
+        return rc;
+    }
+    double inv[18 * 18];
+    if (!coarse_inverse(alpha, H->fp32, km, inv)) {
+        mg_destroy(H);
+        return fail(AAOMG_ERR_BAD_ARG, "coarsest operator is singular");
+    }
+    int64_t n64 = H->fine64.fs;
+    if ((rc = dalloc(H, (void**)&H->ainv, sizeof(inv))) || (rc = dalloc(H, (void**)&H->part, 2 * kResidBlocks * sizeof(double))) ||
+        (rc = dalloc(H, (void**)&H->red, 2 * sizeof(double)))) {
+        mg_destroy(H);
+        return rc;
+    }
+    if (H->fp32 && ((rc = dalloc(H, (void**)&H->x64, 2 * n64 * sizeof(double))) ||
+                    (rc = dalloc(H, (void**)&H->f64, 2 * n64 * sizeof(double))))) {
+        mg_destroy(H);
+        return rc;
+    }
+    if (cudaMallocHost((void**)&H->h_red, 2 * sizeof(double)) != cudaSuccess) {
+        mg_destroy(H);
+        return fail(AAOMG_ERR_OOM, "pinned host allocation");
+    }
+    cudaError_t e = cudaMemcpy(H->ainv, inv, sizeof(inv), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mg_destroy(H);
+        return fail(AAOMG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if ((rc = build_graph(H))) {
+        mg_destroy(H);
+        return rc;
+    }
+    *out = H;
+    return AAOMG_OK;
+}
+
+long long mg_num_nodes(mg_handle h) { return h ? (long long)h->fine64.fs : 0; }
+
+long long mg_kernel_launches(mg_handle h) { return h ? h->launches : 0; }
+
+int mg_rhs_from_yd(mg_handle h, const double* yD, double* f, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!yD || !f) return fail(AAOMG_ERR_BAD_ARG, "null vector");
+    launch_rhs(h->fine64, yD, f, (cudaStream_t)stream);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int mg_residual(mg_handle h, const double* f, const double* x, double* r, double* relres, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !x) return fail(AAOMG_ERR_BAD_ARG, "null vector");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_resid64(h->fine64, f, x, r, nullptr, 0, 0, h->part, kResidBlocks, h->red, s);
+    h->launches += 2;
+    CK(cudaGetLastError());
+    if (relres) {
+        CK(cudaMemcpyAsync(h->h_red, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double fn = h->h_red[1] > 0.0 ? h->h_red[1] : 1.0;
+        *relres = std::sqrt(h->h_red[0] / fn);
+    }
+    return AAOMG_OK;
+}
+
+int mg_smooth(mg_handle h, const double* f, double* x, int steps, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !x || steps < 0) return fail(AAOMG_ERR_BAD_ARG, "null vector or negative steps");
+    if (h->L < 2) return fail(AAOMG_ERR_BAD_ARG, "no smoothing on the coarsest grid (levels = 1)");
+    cudaStream_t s = (cudaStream_t)stream;
+    Lev& v = h->lev[h->L];
+    size_t bytes = (size_t)vec_bytes(h);
+    h->rec_kernels = 0;
+    if (!h->fp32) {
+        CK(cudaMemcpyAsync(v.f, f, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(v.x, x, bytes, cudaMemcpyDeviceToDevice, s));
+        smooth<double>(h, h->L, steps, s);
+        CK(cudaMemcpyAsync(x, v.x, bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+        to_inner(h, f, v.f, h->beta, s);
+        to_inner(h, x, v.x, 1.0 / h->beta, s);
+        smooth<float>(h, h->L, steps, s);
+        launch_to_f64(v.n, (const float*)v.x, v.ld, v.fs, x, h->fine64.ld, h->fine64.fs, h->beta, s);
+        h->rec_kernels += 3;
+    }
+    h->launches += h->rec_kernels;
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int mg_restrict(mg_handle h, const double* f, const double* x, double* fc, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !x || !fc) return fail(AAOMG_ERR_BAD_ARG, "null vector");
+    if (h->L < 2) return fail(AAOMG_ERR_BAD_ARG, "restriction needs levels >= 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    Lev& v = h->lev[h->L];
+    Lev& c = h->lev[h->L - 1];
+    size_t bytes = (size_t)vec_bytes(h);
+    if (!h->fp32) {
+        CK(cudaMemcpyAsync(v.f, f, bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(v.x, x, bytes, cudaMemcpyDeviceToDevice, s));
+        launch_restrict<double>(v.pd, c.pd, (const double*)v.f, (const double*)v.x, (double*)c.f, (double*)c.x, s);
+        CK(cudaMemcpyAsync(fc, c.f, sizeof(double) * 2 * c.fs, cudaMemcpyDeviceToDevice, s));
+        h->launches += 1;
+    } else {
+        to_inner(h, f, v.f, h->beta, s);
+        to_inner(h, x, v.x, 1.0 / h->beta, s);
+        launch_restrict<float>(v.pf, c.pf, (const float*)v.f, (const float*)v.x, (float*)c.f, (float*)c.x, s);
+        launch_to_f64(c.n, (const float*)c.f, c.ld, c.fs, fc, c.n + 1, (int64_t)(c.n + 1) * (c.n + 1), 1.0 / h->beta,
+                      s);
+        h->launches += 4;
+    }
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int mg_prolong_add(mg_handle h, const double* xc, double* x, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!xc || !x) return fail(AAOMG_ERR_BAD_ARG, "null vector");
+    if (h->L < 2) return fail(AAOMG_ERR_BAD_ARG, "prolongation needs levels >= 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    Lev& v = h->lev[h->L];
+    Lev& c = h->lev[h->L - 1];
+    size_t bytes = (size_t)vec_bytes(h);
+    if (!h->fp32) {
+        CK(cudaMemcpyAsync(c.x, xc, sizeof(double) * 2 * c.fs, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(v.x, x, bytes, cudaMemcpyDeviceToDevice, s));
+        launch_prolong<double>(v.pd, c.pd, (const double*)c.x, (double*)v.x, s);
+        CK(cudaMemcpyAsync(x, v.x, bytes, cudaMemcpyDeviceToDevice, s));
+        h->launches += 1;
+    } else {
+        launch_to_f32(c.n, xc, c.n + 1, (int64_t)(c.n + 1) * (c.n + 1), (float*)c.x, c.ld, c.fs, 1.0 / h->beta, s);
+        to_inner(h, x, v.x, 1.0 / h->beta, s);
+        launch_prolong<float>(v.pf, c.pf, (const float*)c.x, (float*)v.x, s);
+        launch_to_f64(v.n, (const float*)v.x, v.ld, v.fs, x, h->fine64.ld, h->fine64.fs, h->beta, s);
+        h->launches += 4;
+    }
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int mg_cycle(mg_handle h, const double* f, double* x, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !x) return fail(AAOMG_ERR_BAD_ARG, "null vector");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)vec_bytes(h);
+    CK(cudaMemcpyAsync(iter_f(h), f, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(iter_x(h), x, bytes, cudaMemcpyDeviceToDevice, s));
+    if (h->fp32) {
+        Lev& v = h->lev[h->L];
+        launch_resid64(h->fine64, iter_f(h), iter_x(h), nullptr, (float*)v.f, v.ld, v.fs, h->part, kResidBlocks, h->red, s);
+        h->launches += 2;
+    }
+    if ((rc = run_iteration(h, s))) return rc;
+    CK(cudaMemcpyAsync(x, iter_x(h), bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int mg_solve(mg_handle h, const double* f, double* x, double tol, int* iters, double* relres, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !x || !(tol >= 0.0)) return fail(AAOMG_ERR_BAD_ARG, "null vector or bad tol");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)vec_bytes(h);
+    CK(cudaMemcpyAsync(iter_f(h), f, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(iter_x(h), x, bytes, cudaMemcpyDeviceToDevice, s));
+    int status = solve_internal(h, tol, iters, relres, s);
+    if (status == AAOMG_ERR_CUDA) return status;
+    CK(cudaMemcpyAsync(x, iter_x(h), bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return status;
+}
+
+int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol, int* iters, double* relres,
+                  void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f_host || !x_host || !(tol >= 0.0)) return fail(AAOMG_ERR_BAD_ARG, "null vector or bad tol");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)vec_bytes(h);
+    CK(cudaMemcpyAsync(iter_f(h), f_host, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(iter_x(h), x_host, bytes, cudaMemcpyHostToDevice, s));
+    int status = solve_internal(h, tol, iters, relres, s);
+    if (status == AAOMG_ERR_CUDA) return status;
+    CK(cudaMemcpyAsync(x_host, iter_x(h), bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return status;
+}
+
+int mg_get_history(mg_handle h, double* buf, int cap, int* n) {
+    if (!h || (!buf && cap > 0)) return fail(AAOMG_ERR_BAD_ARG, "null handle or buffer");
+    int k = (int)h->hist.size() < cap ? (int)h->hist.size() : cap;
+    for (int i = 0; i < k; ++i) buf[i] = h->hist[i];
+    if (n) *n = k;
+    return AAOMG_OK;
+}
+
+}  // extern "C"

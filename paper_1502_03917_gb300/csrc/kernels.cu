@@ -1,0 +1,417 @@
+// kernels.cu -- per-level stencil kernels: residual, NE update, one LSGS colour
+// phase, defect restriction, prolongation, coarsest solve, FP64 refinement and
+// norm reductions.  One thread per node (or per coarse node); the operator is
+// applied matrix-free from the coefficients of common.cuh.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace aaomg {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ bool node_interior(const LevelP<T>& P, int i, int j) {
+    return i > 0 && i < P.n && j > 0 && j < P.n;
+}
+
+template <typename T>
+__device__ __forceinline__ void row_coeffs(const LevelP<T>& P, int i, int j, T m[7], T k[7]) {
+    if (node_interior(P, i, j)) {
+        m[0] = P.mC;
+        k[0] = P.kC;
+#pragma unroll
+        for (int o = 1; o < 7; ++o) {
+            m[o] = P.mO;
+            k[o] = o <= 4 ? P.kE : P.kD;
+        }
+    } else {
+        row_coeffs_general<T>(i, j, P.n, P.h2, P.km, m, k);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_ly(const LevelP<T>& P, int i, int j) {
+    return node_interior(P, i, j) ? P.invLy_int : P.invLy[cls3(i, P.n) + 3 * cls3(j, P.n)];
+}
+
+template <typename T>
+__device__ __forceinline__ bool all_interior(const LevelP<T>& P, int i, int j) {
+    return i >= 2 && i <= P.n - 2 && j >= 2 && j <= P.n - 2;
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_n(const LevelP<T>& P, int field, int i, int j) {
+    if (all_interior(P, i, j)) return field == 0 ? P.invNy_int : P.invNl_int;
+    int c = cls5(i, P.n) + 5 * cls5(j, P.n);
+    return field == 0 ? P.invNy[c] : P.invNl[c];
+}
+
+// v at the 7 offsets of node (i,j); 0 where the offset leaves the grid
+template <typename T>
+__device__ __forceinline__ void load7(const LevelP<T>& P, const T* __restrict__ v, int i, int j, T out[7]) {
+    if (node_interior(P, i, j)) {
+        const T* p = v + (int64_t)j * P.ld + i;
+#pragma unroll
+        for (int o = 0; o < 7; ++o) out[o] = p[DJ(o) * P.ld + DI(o)];
+    } else {
+#pragma unroll
+        for (int o = 0; o < 7; ++o) {
+            int ii = i + DI(o), jj = j + DJ(o);
+            out[o] = in_grid(ii, jj, P.n) ? v[(int64_t)jj * P.ld + ii] : T(0);
+        }
+    }
+}
+
+// (A x) at node (i,j): returns ay = (M y + c K lambda), al = (c K y - d M lambda)
+template <typename T>
+__device__ __forceinline__ void apply_A(const LevelP<T>& P, const T* x, int i, int j, T& ay, T& al) {
+    T m[7], k[7], y[7], l[7];
+    row_coeffs(P, i, j, m, k);
+    load7(P, x, i, j, y);
+    load7(P, x + P.fs, i, j, l);
+    T My = 0, Kl = 0, Ky = 0, Ml = 0;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        My += m[o] * y[o];
+        Kl += k[o] * l[o];
+        Ky += k[o] * y[o];
+        Ml += m[o] * l[o];
+    }
+    ay = My + P.c * Kl;
+    al = P.c * Ky - P.d * Ml;
+}
+
+template <typename T>
+__device__ __forceinline__ int64_t nidx(const LevelP<T>& P, int i, int j) {
+    return (int64_t)j * P.ld + i;
+}
+
+// ---------------------------------------------------------------- kernels --
+
+// rh = L^{-1} (f - A x)
+template <typename T>
+__global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ rh) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > P.n || j > P.n) return;
+    T ay, al;
+    apply_A(P, x, i, j, ay, al);
+    int64_t p = nidx(P, i, j);
+    T il = inv_ly(P, i, j);
+    rh[p] = (f[p] - ay) * il;
+    rh[p + P.fs] = (f[p + P.fs] - al) * (il * P.invd);
+}
+
+// Algorithm 1 update: x += tau L^{-1} A rh (A symmetric), with rh = L^{-1} r
+template <typename T>
+__global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict__ rh) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > P.n || j > P.n) return;
+    T qy, ql;
+    apply_A(P, rh, i, j, qy, ql);
+    int64_t p = nidx(P, i, j);
+    T il = inv_ly(P, i, j);
+    x[p] += P.tau * il * qy;
+    x[p + P.fs] += P.tau * (il * P.invd) * ql;
+}
+
+// One colour phase of Algorithm 2: every unknown of field `field` on a node of
+// colour `colour` does q = sum_j A_ij rh_j, p = q / N_ii, x_i += p and
+// rh_j -= A_ji p / L_jj on its neighbourhood.  Nodes of one colour share no
+// neighbour, so the updates of a phase are independent and race-free.
+template <typename T>
+__global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__ x, T* __restrict__ rh) {
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (j > P.n) return;
+    int i = ((colour - 2 * j) % 7 + 7) % 7 + 7 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i > P.n) return;
+    T m[7], k[7], ry[7], rl[7];
+    row_coeffs(P, i, j, m, k);
+    load7(P, rh, i, j, ry);
+    load7(P, rh + P.fs, i, j, rl);
+    T q = 0;
+    if (field == 0) {
+#pragma unroll
+        for (int o = 0; o < 7; ++o) q += m[o] * ry[o] + P.c * k[o] * rl[o];
+    } else {
+#pragma unroll
+        for (int o = 0; o < 7; ++o) q += P.c * k[o] * ry[o] - P.d * m[o] * rl[o];
+    }
+    T p = q * inv_n(P, field, i, j);
+    x[nidx(P, i, j) + (field ? P.fs : 0)] += p;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        int ii = i + DI(o), jj = j + DJ(o);
+        if (!in_grid(ii, jj, P.n)) continue;
+        T il = inv_ly(P, ii, jj);
+        int64_t q2 = nidx(P, ii, jj);
+        if (field == 0) {
+            rh[q2] = ry[o] - m[o] * p * il;
+            rh[q2 + P.fs] = rl[o] - P.c * k[o] * p * (il * P.invd);
+        } else {
+            rh[q2] = ry[o] - P.c * k[o] * p * il;
+            rh[q2 + P.fs] = rl[o] + m[o] * p * il;
+        }
+    }
+}
+
+// Defect restriction: fc = P^T (f - A x) on a coarse node (I,J) -- weight 1 at
+// the fine node (2I,2J) and 1/2 at its six neighbours, the midpoints of the
+// coarse edges; also zeroes the coarse iterate xc.
+template <typename T>
+__global__ void k_restrict(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ f, const T* __restrict__ x,
+                           T* __restrict__ fc, T* __restrict__ xc) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    int J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I > Pc.n || J > Pc.n) return;
+    T sy = 0, sl = 0;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        int i = 2 * I + DI(o), j = 2 * J + DJ(o);
+        if (!in_grid(i, j, Pf.n)) continue;
+        T ay, al;
+        apply_A(Pf, x, i, j, ay, al);
+        int64_t p = nidx(Pf, i, j);
+        T w = o == 0 ? T(1) : T(0.5);
+        sy += w * (f[p] - ay);
+        sl += w * (f[p + Pf.fs] - al);
+    }
+    int64_t c = nidx(Pc, I, J);
+    fc[c] = sy;
+    fc[c + Pc.fs] = sl;
+    xc[c] = T(0);
+    xc[c + Pc.fs] = T(0);
+}
+
+// x += P xc: nodal interpolation of the coarse P1 function at the fine node
+template <typename T>
+__global__ void k_prolong(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ xc, T* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > Pf.n || j > Pf.n) return;
+    int I = i >> 1, J = j >> 1;
+    int64_t a = nidx(Pc, I, J);
+    int64_t b = a;
+    if ((i & 1) && (j & 1)) b = nidx(Pc, I + 1, J + 1);
+    else if (i & 1) b = nidx(Pc, I + 1, J);
+    else if (j & 1) b = nidx(Pc, I, J + 1);
+    int64_t p = nidx(Pf, i, j);
+    if (a == b) {
+        x[p] += xc[a];
+        x[p + Pf.fs] += xc[a + Pc.fs];
+    } else {
+        x[p] += T(0.5) * (xc[a] + xc[b]);
+        x[p + Pf.fs] += T(0.5) * (xc[a + Pc.fs] + xc[b + Pc.fs]);
+    }
+}
+
+// exact solve on the coarsest grid (18 unknowns): x = A_1^{-1} f in FP64
+template <typename T>
+__global__ void k_coarsest(const double* __restrict__ ainv, const T* __restrict__ f, T* __restrict__ x, int64_t fs) {
+    __shared__ double fb[18];
+    int t = threadIdx.x;
+    if (t < 18) fb[t] = (double)f[(t < 9 ? t : fs + t - 9)];
+    __syncthreads();
+    if (t < 18) {
+        double s = 0.0;
+        for (int c = 0; c < 18; ++c) s += ainv[t * 18 + c] * fb[c];
+        x[(t < 9 ? t : fs + t - 9)] = (T)s;
+    }
+}
+
+// ---------------------------------------------------------- reductions --
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sum of two values; result valid in thread 0
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[32], sb[32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        a = l < nw ? sa[l] : 0.0;
+        b = l < nw ? sb[l] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+}
+
+// FP64 residual r = f - A x on the paper's system (c = 1, d = 1/alpha) with
+// ||r||^2_{L^-1} and ||f||^2_{L^-1} partial sums per block.  Optional outputs:
+// r (FP64) and the scaled single-precision defect fin = (r_y, beta r_lambda)
+// for the FP32 cycles.
+__global__ void k_resid64(LevelP<double> P, const double* __restrict__ f, const double* __restrict__ x,
+                          double* __restrict__ r, float* __restrict__ fin, int64_t fin_ld, int64_t fin_fs,
+                          double* __restrict__ part) {
+    int64_t nn = (int64_t)(P.n + 1) * (P.n + 1);
+    double srr = 0.0, sff = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(t / (P.n + 1)), i = (int)(t - (int64_t)j * (P.n + 1));
+        double ay, al;
+        apply_A(P, x, i, j, ay, al);
+        int64_t p = nidx(P, i, j);
+        double fy = f[p], fl = f[p + P.fs];
+        double ry = fy - ay, rl = fl - al;
+        double il = inv_ly(P, i, j), ill = il * P.invd;
+        srr += ry * ry * il + rl * rl * ill;
+        sff += fy * fy * il + fl * fl * ill;
+        if (r) {
+            r[p] = ry;
+            r[p + P.fs] = rl;
+        }
+        if (fin) {
+            int64_t q = (int64_t)j * fin_ld + i;
+            fin[q] = (float)ry;
+            fin[q + fin_fs] = (float)(P.beta * rl);
+        }
+    }
+    block_sum2(srr, sff);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = srr;
+        part[2 * blockIdx.x + 1] = sff;
+    }
+}
+
+// sum the per-block partials in a fixed order (deterministic)
+__global__ void k_reduce_parts(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
+        a += part[2 * t];
+        b += part[2 * t + 1];
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+// x += S^{-1} d: y += d_y, lambda += beta d_lambda (undo the FP32 scaling)
+__global__ void k_refine_update(LevelP<double> P, double* __restrict__ x, const float* __restrict__ d, int64_t d_ld,
+                                int64_t d_fs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > P.n || j > P.n) return;
+    int64_t p = nidx(P, i, j), q = (int64_t)j * d_ld + i;
+    x[p] += (double)d[q];
+    x[p + P.fs] += P.beta * (double)d[q + d_fs];
+}
+
+// v (paper's scaling, FP64) -> out (FP32 symmetric scaling): lambda * s_l
+__global__ void k_to_f32(int n, const double* __restrict__ v, int64_t v_ld, int64_t v_fs, float* __restrict__ out,
+                         int64_t o_ld, int64_t o_fs, double s_l) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > n || j > n) return;
+    int64_t p = (int64_t)j * v_ld + i, q = (int64_t)j * o_ld + i;
+    out[q] = (float)v[p];
+    out[q + o_fs] = (float)(v[p + v_fs] * s_l);
+}
+
+__global__ void k_to_f64(int n, const float* __restrict__ v, int64_t v_ld, int64_t v_fs, double* __restrict__ out,
+                         int64_t o_ld, int64_t o_fs, double s_l) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > n || j > n) return;
+    int64_t p = (int64_t)j * v_ld + i, q = (int64_t)j * o_ld + i;
+    out[q] = (double)v[p];
+    out[q + o_fs] = (double)v[p + v_fs] * s_l;
+}
+
+// f = (M yD, 0)
+__global__ void k_rhs(LevelP<double> P, const double* __restrict__ yD, double* __restrict__ f) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > P.n || j > P.n) return;
+    double m[7], k[7], y[7];
+    row_coeffs(P, i, j, m, k);
+    // yD is packed with stride n+1
+    LevelP<double> Q = P;
+    Q.ld = P.n + 1;
+    load7(Q, yD, i, j, y);
+    double s = 0.0;
+    for (int o = 0; o < 7; ++o) s += m[o] * y[o];
+    int64_t p = nidx(P, i, j);
+    f[p] = s;
+    f[p + P.fs] = 0.0;
+}
+
+inline dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers --
+const dim3 kBlk2(32, 8);
+
+template <typename T>
+void launch_resid_hat(const LevelP<T>& P, const T* f, const T* x, T* rh, cudaStream_t s) {
+    k_resid_hat<T><<<grid2(P.n + 1, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, f, x, rh);
+}
+template <typename T>
+void launch_ne_update(const LevelP<T>& P, T* x, const T* rh, cudaStream_t s) {
+    k_ne_update<T><<<grid2(P.n + 1, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, x, rh);
+}
+template <typename T>
+void launch_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, T* rh, cudaStream_t s) {
+    k_lsgs_phase<T><<<grid2((P.n + 7) / 7, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, field, colour, x, rh);
+}
+template <typename T>
+void launch_restrict(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* f, const T* x, T* fc, T* xc, cudaStream_t s) {
+    k_restrict<T><<<grid2(Pc.n + 1, Pc.n + 1, kBlk2), kBlk2, 0, s>>>(Pf, Pc, f, x, fc, xc);
+}
+template <typename T>
+void launch_prolong(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* xc, T* x, cudaStream_t s) {
+    k_prolong<T><<<grid2(Pf.n + 1, Pf.n + 1, kBlk2), kBlk2, 0, s>>>(Pf, Pc, xc, x);
+}
+template <typename T>
+void launch_coarsest(const double* ainv, const T* f, T* x, int64_t fs, cudaStream_t s) {
+    k_coarsest<T><<<1, 32, 0, s>>>(ainv, f, x, fs);
+}
+
+void launch_resid64(const LevelP<double>& P, const double* f, const double* x, double* r, float* fin, int64_t fin_ld,
+                    int64_t fin_fs, double* part, int nblk, double* out, cudaStream_t s) {
+    k_resid64<<<nblk, 256, 0, s>>>(P, f, x, r, fin, fin_ld, fin_fs, part);
+    k_reduce_parts<<<1, 256, 0, s>>>(part, nblk, out);
+}
+void launch_refine_update(const LevelP<double>& P, double* x, const float* d, int64_t d_ld, int64_t d_fs,
+                          cudaStream_t s) {
+    k_refine_update<<<grid2(P.n + 1, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, x, d, d_ld, d_fs);
+}
+void launch_to_f32(int n, const double* v, int64_t v_ld, int64_t v_fs, float* out, int64_t o_ld, int64_t o_fs,
+                   double s_l, cudaStream_t s) {
+    k_to_f32<<<grid2(n + 1, n + 1, kBlk2), kBlk2, 0, s>>>(n, v, v_ld, v_fs, out, o_ld, o_fs, s_l);
+}
+void launch_to_f64(int n, const float* v, int64_t v_ld, int64_t v_fs, double* out, int64_t o_ld, int64_t o_fs,
+                   double s_l, cudaStream_t s) {
+    k_to_f64<<<grid2(n + 1, n + 1, kBlk2), kBlk2, 0, s>>>(n, v, v_ld, v_fs, out, o_ld, o_fs, s_l);
+}
+void launch_rhs(const LevelP<double>& P, const double* yD, double* f, cudaStream_t s) {
+    k_rhs<<<grid2(P.n + 1, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, yD, f);
+}
+
+#define AAOMG_INST(T)                                                                                          \
+    template void launch_resid_hat<T>(const LevelP<T>&, const T*, const T*, T*, cudaStream_t);                \
+    template void launch_ne_update<T>(const LevelP<T>&, T*, const T*, cudaStream_t);                          \
+    template void launch_lsgs_phase<T>(const LevelP<T>&, int, int, T*, T*, cudaStream_t);                     \
+    template void launch_restrict<T>(const LevelP<T>&, const LevelP<T>&, const T*, const T*, T*, T*,          \
+                                     cudaStream_t);                                                           \
+    template void launch_prolong<T>(const LevelP<T>&, const LevelP<T>&, const T*, T*, cudaStream_t);          \
+    template void launch_coarsest<T>(const double*, const T*, T*, int64_t, cudaStream_t);
+AAOMG_INST(float)
+AAOMG_INST(double)
+
+}  // namespace aaomg

@@ -1,0 +1,204 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the
+C ABI, element by element, on seeded inputs.
+
+Tolerances: FP64 path 1e-12 relative difference per step (sum-order rounding
+only), FP32 path 1e-5 per step (single-precision rounding of a handful of
+operations per unknown), solutions 1e-8 relative error (solved to a relative
+residual of 1e-11 so that the error bound holds for every alpha).
+"""
+import numpy as np
+import pytest
+
+from paper_1502_03917_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32_refine": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def mg():
+    import paper_1502_03917_gb300.aaomg as m
+
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def field_reldiff(a, b, n):
+    """max over the two fields of ||a - b|| / ||b||"""
+    out = 0.0
+    for s in (slice(0, n), slice(n, 2 * n)):
+        nb = np.linalg.norm(b[s])
+        out = max(out, np.linalg.norm(a[s] - b[s]) / (nb if nb > 0 else 1.0))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("L", [2, 3, 5, 7])
+@pytest.mark.parametrize("alpha", [1.0, 1e-4, 1e-8])
+def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 100 + L))
+    f = inputs.f32_exact(inputs.x_uniform(L, 200 + L))
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother)
+    n = o.nn()
+    with mg.Solver(L, alpha, smoother=smoother, precision=precision) as s:
+        for steps in (1, 2):
+            x = dev(x0)
+            s.smooth(dev(f), x, steps)
+            got = host(x)
+            want = o.smooth(f, x0, steps)
+            d = field_reldiff(got, want, n)
+            assert d <= TOL[precision], (steps, d)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("L", [2, 4, 7])
+def test_transfer_parity(mg, oracle_mod, L, precision):
+    alpha = 1e-3
+    o = oracle_mod.Oracle(L, alpha)
+    n, nc = o.nn(L), o.nn(L - 1)
+    x = inputs.f32_exact(inputs.x_uniform(L, 7))
+    f = inputs.f32_exact(inputs.x_uniform(L, 8))
+    xc = inputs.f32_exact(inputs.x_uniform(L - 1, 9))
+    with mg.Solver(L, alpha, precision=precision) as s:
+        fc = host(s.restrict(dev(f), dev(x)))
+        want = o.restrict(o.residual(f, x))
+        assert field_reldiff(fc, want, nc) <= TOL[precision]
+        xg = dev(x)
+        s.prolong_add(dev(xc), xg)
+        assert field_reldiff(host(xg), o.prolong_add(xc, x), n) <= TOL[precision]
+
+
+@pytest.mark.parametrize("L", [1, 3, 6])
+def test_residual_and_rhs_parity(mg, oracle_mod, L):
+    alpha = 1e-5
+    o = oracle_mod.Oracle(L, alpha)
+    n = o.nn()
+    yD = inputs.yd_sine_noise(L, 1)
+    x = inputs.x_uniform(L, 3)
+    with mg.Solver(L, alpha) as s:
+        f = s.rhs_from_yd(dev(yD))
+        fo = o.rhs(yD)
+        assert np.linalg.norm(host(f)[:n] - fo[:n]) / np.linalg.norm(fo[:n]) <= 1e-13
+        assert np.all(host(f)[n:] == 0.0)
+        r = torch.empty_like(f)
+        rr = s.residual(f, dev(x), r)
+        ro = o.residual(fo, x)
+        assert np.linalg.norm(host(r) - ro) / np.linalg.norm(ro) <= 1e-13
+        assert rr == pytest.approx(o.norm_Linv(ro) / o.norm_Linv(fo), rel=1e-12)
+
+
+@pytest.mark.parametrize("cycle", ["W", "V"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs"])
+@pytest.mark.parametrize("L", [1, 2, 4, 6])
+def test_cycle_parity_fp64(mg, oracle_mod, L, smoother, cycle):
+    alpha = 1e-2
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother, gamma=2 if cycle == "W" else 1)
+    f = o.rhs(inputs.yd_uniform(L, 0))
+    x0 = inputs.x_uniform(L, 4)
+    with mg.Solver(L, alpha, smoother=smoother, cycle=cycle) as s:
+        x = dev(x0)
+        s.cycle(dev(f), x)
+        want = o.cycle(f, x0)
+        assert field_reldiff(host(x), want, o.nn()) <= 1e-12
+
+
+def solution_errors(o, x, xo):
+    n = o.nn()
+    eL = o.norm_L(x - xo) / o.norm_L(xo)
+    ey = np.abs(x[:n] - xo[:n]).max() / np.abs(xo[:n]).max()
+    eu = np.abs(x[n:] - xo[n:]).max() / np.abs(xo[n:]).max()  # u = lambda / alpha: same relative error
+    return max(eL, ey, eu)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs"])
+@pytest.mark.parametrize("alpha", [1.0, 1e-2, 1e-4, 1e-6, 1e-8])
+def test_solve_parity_L5(mg, oracle_mod, alpha, smoother, precision):
+    L = 5
+    yD = inputs.yd_uniform(L, 0)
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother)
+    fo = o.rhs(yD)
+    xo, ito, _, _ = o.solve(fo, tol=1e-13, max_iter=400)
+    with mg.Solver(L, alpha, smoother=smoother, precision=precision, max_iter=200) as s:
+        f = s.rhs_from_yd(dev(yD))
+        x = torch.zeros_like(f)
+        it, rr, _ = s.solve(f, x, tol=1e-11)
+        assert rr <= 1e-11
+        assert solution_errors(o, host(x), xo) <= 1e-8
+        if precision == "fp64":
+            # same iterates as the oracle: identical iteration count to the same tolerance
+            _, it_o, _, _ = o.solve(fo, tol=1e-11)
+            assert it == it_o
+
+
+def test_solve_host_and_history(mg, oracle_mod):
+    L, alpha = 4, 1e-3
+    o = oracle_mod.Oracle(L, alpha, smoother="lsgs")
+    f = o.rhs(inputs.yd_uniform(L, 1))
+    xo, _, _, hist_o = o.solve(f, tol=1e-10)
+    with mg.Solver(L, alpha, smoother="lsgs") as s:
+        x = np.zeros_like(f)
+        it, rr, _ = s.solve_host(np.ascontiguousarray(f), x, tol=1e-10)
+        assert solution_errors(o, x, xo) <= 1e-8
+        h = s.history()
+        assert len(h) == it + 1
+        np.testing.assert_allclose(h, hist_o, rtol=1e-9)
+
+
+def test_determinism(mg):
+    L, alpha = 6, 1e-4
+    yD = dev(inputs.yd_uniform(L, 3))
+    outs = []
+    for _ in range(2):
+        with mg.Solver(L, alpha, smoother="lsgs", precision="fp32_refine") as s:
+            f = s.rhs_from_yd(yD)
+            x = torch.zeros_like(f)
+            s.solve(f, x, tol=1e-10)
+            outs.append(host(x))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_bad_arguments(mg):
+    for args in ((0, 1.0), (14, 1.0), (5, 0.0), (5, -1.0), (5, float("nan")), (5, float("inf"))):
+        with pytest.raises(mg.MGError) as e:
+            mg.Solver(*args)
+        assert e.value.code == mg.ERR_BAD_ARG
+    with mg.Solver(3, 1.0) as s:
+        lib = mg.load()
+        assert lib.mg_solve(s._h, None, None, 1e-8, None, None, None) == mg.ERR_BAD_ARG
+        assert lib.mg_smooth(None, None, None, 1, None) == mg.ERR_BAD_ARG
+
+
+def test_not_converged_and_nan(mg):
+    L = 5
+    with mg.Solver(L, 1e-2, smoother="ne", max_iter=2) as s:
+        f = s.rhs_from_yd(dev(inputs.yd_uniform(L, 0)))
+        x = torch.zeros_like(f)
+        it, rr, code = s.solve(f, x, tol=1e-12, raise_on_fail=False)
+        assert code == mg.ERR_NOT_CONVERGED and it == 2
+        x[5] = float("nan")
+        it, rr, code = s.solve(f, x, tol=1e-12, raise_on_fail=False)
+        assert code == mg.ERR_DIVERGED
+
+
+def test_constant_desired_state(mg):
+    L, alpha, c = 6, 1e-3, -0.4
+    with mg.Solver(L, alpha, smoother="lsgs", precision="fp32_refine") as s:
+        f = s.rhs_from_yd(torch.full((s.N,), c, dtype=torch.float64, device="cuda"))
+        x = torch.zeros_like(f)
+        s.solve(f, x, tol=1e-12)
+        xh = host(x)
+        np.testing.assert_allclose(xh[: s.N], c / (1 + alpha), rtol=1e-9)
+        np.testing.assert_allclose(xh[s.N:], alpha * c / (1 + alpha), rtol=1e-8)
