@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the all-at-once multigrid solver for the Poisson control problem.
+
+Workload (one "step"): the scaling configuration at its largest size -- unit
+square, h = 2^-11 (2049 x 2049 nodes, 8.4M unknowns y and lambda), y_D =
+sin(2 pi x) sin(2 pi y) + 0.1 N(0,1) (seed 1), one solve from x = 0 to a
+relative residual of 1e-8 for each alpha in {1, 1e-2, 1e-4, 1e-6, 1e-8}, with
+the LSGS smoother, W-cycle, 2+2 steps, down to h = 1/2, FP32 cycles inside FP64
+iterative refinement.  Inputs are resident in HBM when timing starts; L2 is
+flushed (256 MB write) before every timed step.
+
+Printed JSON line: value = solved unknowns/s over all ranks; fp64_plain = the
+same workload with every operation in FP64; e2e = through mg_solve_host with
+pinned host buffers (copies inside the timed region); roofline = the
+finest-level smoother sweeps (CUDA events inside the solve) against the
+measured HBM copy bandwidth; cpu_baseline = the FP64 CPU oracle on a bounded
+sample.  `--impl reference` times the CPU oracle alone on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ALPHAS = [1.0, 1e-2, 1e-4, 1e-6, 1e-8]
+METRIC = "solved unknowns/s at 1e-8 rel. residual, FP32+refine vs FP64; smoother GB/s"
+UNIT = "unknowns/s"
+SWEEP_BYTES_FP32 = 24  # per node and sweep: read y, lambda, f_y, f_lambda; write y, lambda (4 B each)
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_L{L}.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--level", type=int, default=11)
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--smoother", default="lsgs", choices=["ne", "lsgs", "slsgs"])
+    p.add_argument("--cycle", default="W", choices=["V", "W"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200", "-i",
+                 str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- our arm ----
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1502_03917_gb300 import build as B
+    from paper_1502_03917_gb300 import inputs
+    import paper_1502_03917_gb300.aaomg as mg
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    L = args.level
+    yD = torch.tensor(inputs.yd_sine_noise(L, 1), dtype=torch.float64, device="cuda")
+
+    def make(precision, profile):
+        return {a: mg.Solver(L, a, smoother=args.smoother, precision=precision, cycle=args.cycle, max_iter=100,
+                             profile=profile) for a in ALPHAS}
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    def timed_steps(solvers, K, W):
+        fs = {a: s.rhs_from_yd(yD) for a, s in solvers.items()}
+        xs = {a: torch.zeros_like(fs[a]) for a in solvers}
+        its = {}
+
+        def step():
+            for a, s in solvers.items():
+                xs[a].zero_()
+                it, rr, code = s.solve(fs[a], xs[a], tol=args.tol)
+                its[a] = it
+
+        for _ in range(W):
+            step()
+        for s in solvers.values():
+            s.reset_profile()
+        l0 = sum(s.launches() for s in solvers.values())
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        clk = ClockSampler(local)
+        clk.start()
+        for k in range(K):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            step()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        launches = sum(s.launches() for s in solvers.values()) - l0
+        prof = [s.profile() for s in solvers.values()]
+        return ms, its, launches, prof, clocks, xs
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    K, W = args.steps, args.warmup
+    N = ((1 << L) + 1) ** 2
+    unknowns_step = len(ALPHAS) * 2 * N
+
+    sol32 = make("fp32_refine", True)
+    ms, its32, launches, prof, clocks, xs32 = timed_steps(sol32, K, W)
+    ms = max_over_ranks(ms)
+    value = world * unknowns_step * K / (ms / 1e3)
+
+    # roofline of the dominant kernel: the finest-level smoother sweeps
+    pk = peaks()
+    sm_ms = sum(p[0] for p in prof)
+    sweeps = sum(p[1] for p in prof)
+    achieved = SWEEP_BYTES_FP32 * N * sweeps / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "finest-level LSGS smoothing sweep (FP32)",
+                "peak_source": "measured" if pk else "fallback",
+                "sweep_ms": sm_ms / sweeps if sweeps else None,
+                "share_of_step": sm_ms / ms if ms else None}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": f"Poisson control, h=2^-{L} ({(1 << L) + 1}^2 nodes, {2 * N} unknowns), "
+                                  f"alpha in {ALPHAS}, y_D=sin(2pi x)sin(2pi y)+0.1N(0,1) seed 1, "
+                                  f"{args.smoother.upper()} {args.cycle}(2,2) to h=1/2, FP32 cycles in FP64 "
+                                  f"refinement, tol {args.tol}",
+                      "level": L, "unknowns_per_solve": 2 * N, "solves_per_step": len(ALPHAS),
+                      "smoother": args.smoother, "cycle": args.cycle, "precision": "fp32_refine",
+                      "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+           "iterations": {str(a): its32[a] for a in ALPHAS},
+           "roofline": roofline, "clocks": clocks, "gpu_launches": launches}
+
+    if not args.no_fp64:
+        sol64 = make("fp64", False)
+        K64 = max(1, min(K, 2))
+        ms64, its64, _, _, _, xs64 = timed_steps(sol64, K64, 1)
+        ms64 = max_over_ranks(ms64)
+        # error of the FP32+refine solutions against the FP64 ones (both at tol)
+        err = 0.0
+        for a in ALPHAS:
+            d = (xs32[a] - xs64[a]).norm() / xs64[a].norm()
+            err = max(err, float(d))
+        out["fp64_plain"] = {"value": world * unknowns_step * K64 / (ms64 / 1e3), "ms_per_step": ms64 / K64,
+                             "iterations": {str(a): its64[a] for a in ALPHAS},
+                             "max_rel_diff_fp32refine_vs_fp64": err}
+        for s in sol64.values():
+            s.close()
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, sol32, yD, K, world, max_over_ranks)
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(L, args, its_gpu=out.get("fp64_plain", {}).get("iterations"))
+    for s in sol32.values():
+        s.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, solvers, yD, K, world, max_over_ranks):
+    """Same metric through mg_solve_host: f and x in pinned host memory, the
+    host-to-device and device-to-host copies inside the timed region."""
+    import torch
+
+    N = next(iter(solvers.values())).N
+    host_f = {}
+    for a, s in solvers.items():
+        f = s.rhs_from_yd(yD)
+        hf = torch.empty(2 * N, dtype=torch.float64, pin_memory=True)
+        hf.copy_(f)
+        host_f[a] = hf
+    hx = torch.empty(2 * N, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+
+    def step():
+        for a, s in solvers.items():
+            hx.zero_()
+            s.solve_host(host_f[a].numpy(), hx.numpy(), tol=args.tol)
+
+    step()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        step()
+    torch.cuda.synchronize()
+    sec = max_over_ranks(time.perf_counter() - t0)
+    n = len(solvers)
+    return {"value": world * n * 2 * N * K / sec, "unit": UNIT, "h2d_bytes_per_step": n * 2 * (2 * N * 8),
+            "d2h_bytes_per_step": n * 2 * N * 8, "ms_per_step": 1e3 * sec / K}
+
+
+def oracle_iterations(L, smoother, tol):
+    """Iteration counts of the FP64 oracle to `tol`, from the committed
+    full-size reference file (written by oracle/make_golden.py)."""
+    try:
+        g = json.load(open(GOLDEN.format(L=L)))
+    except (OSError, ValueError):
+        return None
+    out = {}
+    for r in g["runs"]:
+        if r["smoother"] == smoother:
+            h = r["history"]
+            out[str(r["alpha"])] = next((i for i, v in enumerate(h) if v <= tol), None)
+    return out if out and None not in out.values() else None
+
+
+def cpu_baseline(L, args, its_gpu=None):
+    """The FP64 CPU oracle (single-threaded C) timed on one W-cycle of the same
+    workload (alpha = 1e-4), scaled by the oracle's iteration counts to the
+    tolerance for the five alphas."""
+    import numpy as np
+
+    import oracle
+    from paper_1502_03917_gb300 import inputs
+
+    oracle.build()
+    its = oracle_iterations(L, args.smoother, args.tol) or its_gpu
+    o = oracle.Oracle(L, 1e-4, smoother=args.smoother, gamma=2 if args.cycle == "W" else 1)
+    f = o.rhs(inputs.yd_sine_noise(L, 1))
+    x = np.zeros_like(f)
+    t0 = time.perf_counter()
+    o.cycle(f, x)
+    t_cycle = time.perf_counter() - t0
+    o.close()
+    N = ((1 << L) + 1) ** 2
+    total_it = sum(its.values()) if its else None
+    value = len(ALPHAS) * 2 * N / (t_cycle * total_it) if total_it else None
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one {args.smoother.upper()} {args.cycle}(2,2) cycle at h=2^-{L}, alpha=1e-4, from x=0 "
+                      f"({t_cycle:.2f} s), scaled by the oracle's iteration counts to {args.tol} for the five "
+                      f"alphas ({total_it} cycles); assembly excluded",
+            "seconds_per_cycle": t_cycle}
+
+
+# ------------------------------------------------------------ reference arm --
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1502_03917_gb300 import inputs
+
+    oracle.build()
+    L = args.level
+    N = ((1 << L) + 1) ** 2
+    its = oracle_iterations(L, args.smoother, args.tol)
+    if its is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration counts for h=2^-{L}"}))
+        return
+    yD = inputs.yd_sine_noise(L, 1)
+    # one oracle W-cycle per step, alphas in turn; each step stands for one
+    # solve: (cycle time) x (iterations the oracle needs for that alpha)
+    hier = {}
+    times = []
+    for k in range(args.warmup + args.steps):
+        a = ALPHAS[k % len(ALPHAS)]
+        if a not in hier:
+            o = oracle.Oracle(L, a, smoother=args.smoother, gamma=2 if args.cycle == "W" else 1)
+            hier[a] = (o, o.rhs(yD))
+        o, f = hier[a]
+        x = np.zeros_like(f)
+        t0 = time.perf_counter()
+        o.cycle(f, x)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt * its[str(a)])
+    sec = sum(times)
+    value = args.steps * 2 * N / sec
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"Poisson control, h=2^-{L}, alpha in {ALPHAS}, {args.smoother.upper()} "
+                                  f"{args.cycle}(2,2), FP64 CPU oracle", "level": L},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "per step one oracle cycle at full size, scaled by the oracle's iteration "
+                                      "count for that alpha"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -87,6 +87,7 @@ typedef struct mg_options {
     int max_iter;     /* mg_solve iteration cap; <= 0: 100 */
     int inner_cycles; /* FP32_REFINE: FP32 cycles per refinement step; <= 0: 3 */
     int coarse_level; /* levels <= this run inside one single-block kernel; < 0: default, 0: none */
+    int profile;      /* 1: time the finest-level smoothing inside every iteration (CUDA events) */
 } mg_options;
 
 /* Build the hierarchy for h = 2^-levels (1 <= levels <= 13; level 1 is the
@@ -147,6 +148,13 @@ AAOMG_API int mg_solve_host(mg_handle h, const double* f_host, double* x_host, d
 /* Relative residual after each iteration of the last mg_solve: buf[0] is the
  * initial one; *n receives the count written (<= cap). */
 AAOMG_API int mg_get_history(mg_handle h, double* buf, int cap, int* n);
+
+/* With opt.profile = 1: total device time (ms) of the finest-level smoothing
+ * steps inside the iterations run since the last mg_reset_profile, and the
+ * number of smoothing steps (sweeps) it covers; measured with CUDA events on
+ * the stream the kernels run on. */
+AAOMG_API int mg_get_profile(mg_handle h, double* smooth_ms, long long* sweeps);
+AAOMG_API int mg_reset_profile(mg_handle h);
 
 /* Kernel launches issued by this handle since it was created (for reports). */
 AAOMG_API long long mg_kernel_launches(mg_handle h);

@@ -45,6 +45,7 @@ class Options(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("inner_cycles", ctypes.c_int),
         ("coarse_level", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -80,6 +81,8 @@ def load():
             "mg_solve_host": (I, [H, P, P, D, pI, pD, P]),
             "mg_get_history": (I, [H, pD, I, pI]),
             "mg_kernel_launches": (ctypes.c_longlong, [H]),
+            "mg_get_profile": (I, [H, pD, ctypes.POINTER(ctypes.c_longlong)]),
+            "mg_reset_profile": (I, [H]),
             "mg_strerror": (ctypes.c_char_p, [I]),
             "mg_last_error": (ctypes.c_char_p, []),
         }
@@ -119,12 +122,13 @@ class Solver:
 
     def __init__(self, levels: int, alpha: float, smoother: str = "lsgs", precision: str = "fp64",
                  cycle: str = "W", nu_pre: int = 0, nu_post: int = 0, tau: float = 0.0, k_variant: int = 0,
-                 max_iter: int = 0, inner_cycles: int = 0, coarse_level: int = -1):
+                 max_iter: int = 0, inner_cycles: int = 0, coarse_level: int = -1, profile: bool = False):
         self._lib = load()
         self.levels, self.alpha = int(levels), float(alpha)
         self.smoother, self.precision, self.cycle_kind = smoother, precision, cycle
         opt = Options(SMOOTHER[smoother], int(nu_pre), int(nu_post), CYCLE[cycle], PRECISION[precision],
-                      float(tau), int(k_variant), int(max_iter), int(inner_cycles), int(coarse_level))
+                      float(tau), int(k_variant), int(max_iter), int(inner_cycles), int(coarse_level),
+                      int(bool(profile)))
         h = ctypes.c_void_p()
         _check(self._lib.mg_setup(self.levels, self.alpha, ctypes.byref(opt), ctypes.byref(h)), "mg_setup")
         self._h = h
@@ -214,6 +218,16 @@ class Solver:
         n = ctypes.c_int()
         _check(self._lib.mg_get_history(self._h, buf, 1024, ctypes.byref(n)), "mg_get_history")
         return [buf[i] for i in range(n.value)]
+
+    def profile(self):
+        """(ms, sweeps): device time of the finest-level smoothing inside the
+        iterations since the last reset, and the sweeps it covers."""
+        ms, sw = ctypes.c_double(), ctypes.c_longlong()
+        _check(self._lib.mg_get_profile(self._h, ctypes.byref(ms), ctypes.byref(sw)), "mg_get_profile")
+        return ms.value, sw.value
+
+    def reset_profile(self):
+        _check(self._lib.mg_reset_profile(self._h), "mg_reset_profile")
 
     def launches(self) -> int:
         return int(self._lib.mg_kernel_launches(self._h))

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "aaomg.h"
+#include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
 
@@ -44,6 +45,8 @@ struct Lev {
 
 template <typename T>
 const LevelP<T>& lp(const Lev& v);
+template <typename T>
+const CtaParams<T>& ctap(const mg_ctx* H);
 template <>
 const LevelP<float>& lp<float>(const Lev& v) {
     return v.pf;
@@ -70,14 +73,19 @@ LevelP<T> make_params(int n, int ld, int64_t fs, double alpha, bool scaled, doub
     P.beta = (T)beta;
     P.km = (T)km;
     P.tau = (T)tau;
+    auto coeffs = [&](int i, int j, double m[7], double k[7]) {
+        double kd[7];
+        row_coeffs_general<double>(i, j, n, h2, m, kd);
+        for (int o = 0; o < 7; ++o) k[o] = kd[o] + km * m[o];
+    };
     auto Ly = [&](int i, int j) {
         double m[7], k[7];
-        row_coeffs_general<double>(i, j, n, h2, km, m, k);
+        coeffs(i, j, m, k);
         return m[0] + beta * k[0];
     };
     auto Nd = [&](int i, int j, int field) {
         double m[7], k[7], s = 0.0;
-        row_coeffs_general<double>(i, j, n, h2, km, m, k);
+        coeffs(i, j, m, k);
         for (int o = 0; o < 7; ++o) {
             int ii = i + DI(o), jj = j + DJ(o);
             if (!in_grid(ii, jj, n)) continue;
@@ -87,13 +95,10 @@ LevelP<T> make_params(int n, int ld, int64_t fs, double alpha, bool scaled, doub
         return s;
     };
     {
-        double m[7], k[7];
-        row_coeffs_general<double>(1, 1, n, h2, km, m, k);
+        double m[7], kd[7];
+        row_coeffs_general<double>(1, 1, n, h2, m, kd);
         P.mC = (T)m[0];
         P.mO = (T)m[1];
-        P.kC = (T)k[0];
-        P.kE = (T)k[1];
-        P.kD = (T)k[5];
         P.invLy_int = (T)(1.0 / Ly(1, 1));
     }
     const int rep3[3] = {0, 1, n};
@@ -123,7 +128,8 @@ bool coarse_inverse(double alpha, bool scaled, double km, double* inv) {
     for (int j = 0; j <= n; ++j)
         for (int i = 0; i <= n; ++i) {
             double mm[7], kk[7];
-            row_coeffs_general<double>(i, j, n, h2, km, mm, kk);
+            row_coeffs_general<double>(i, j, n, h2, mm, kk);
+            for (int o = 0; o < 7; ++o) kk[o] += km * mm[o];
             int p = j * 3 + i;
             for (int o = 0; o < 7; ++o) {
                 int ii = i + DI(o), jj = j + DJ(o);
@@ -165,6 +171,9 @@ struct mg_ctx {
     int dev = 0;
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
+    int lc = 0;               // levels <= lc run inside the single-block coarse kernel
+    CtaParams<float> cf{};
+    CtaParams<double> cd{};
     LevelP<double> fine64{};  // the paper's system on the finest level, user layout
     double* x64 = nullptr;    // FP64 finest iterate and right-hand side (internal copies)
     double* f64 = nullptr;
@@ -180,9 +189,42 @@ struct mg_ctx {
     long long rec_kernels = 0;
     std::vector<double> hist;
     std::vector<void*> allocs;
+    // profiling: event pairs around the finest-level smoothing in the graph
+    std::vector<cudaEvent_t> pev;
+    int pev_used = 0;
+    bool recording = false;
+    bool pending = false;  // a graph launch whose events are not yet read
+    double prof_ms = 0.0;
+    long long prof_sweeps = 0, sweeps_per_iter = 0;
 };
 
 namespace {
+
+template <>
+const CtaParams<float>& ctap<float>(const mg_ctx* H) {
+    return H->cf;
+}
+template <>
+const CtaParams<double>& ctap<double>(const mg_ctx* H) {
+    return H->cd;
+}
+
+template <typename T>
+CtaParams<T> make_cta(const mg_ctx* H, int lc, bool scaled, double km) {
+    CtaParams<T> C{};
+    C.lc = lc;
+    for (int l = 1; l <= lc; ++l) {
+        int n = 1 << l;
+        C.P[l] = make_params<T>(n, n + 1, (int64_t)(n + 1) * (n + 1), H->alpha, scaled, km, H->o.tau);
+    }
+    C.smoother = H->o.smoother;
+    C.nu_pre = H->o.nu_pre;
+    C.nu_post = H->o.nu_post;
+    C.gamma = H->o.cycle;
+    C.g_ld = H->lev[lc].ld;
+    C.g_fs = H->lev[lc].fs;
+    return C;
+}
 
 int dalloc(mg_ctx* H, void** p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -218,11 +260,11 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
         H->rec_kernels += 1;
         for (int m = 0; m < steps; ++m) {
             for (int field = 0; field < 2; ++field)
-                for (int c = 0; c < 7; ++c) launch_lsgs_phase<T>(P, field, kColourSeq[c], x, rh, s);
+                for (int c = 0; c < 7; ++c) launch_lsgs_phase<T>(P, field, colour_seq(c), x, rh, s);
             H->rec_kernels += 14;
             if (H->o.smoother == MG_SMOOTHER_SLSGS) {
                 for (int field = 1; field >= 0; --field)
-                    for (int c = 6; c >= 0; --c) launch_lsgs_phase<T>(P, field, kColourSeq[c], x, rh, s);
+                    for (int c = 6; c >= 0; --c) launch_lsgs_phase<T>(P, field, colour_seq(c), x, rh, s);
                 H->rec_kernels += 14;
             }
         }
@@ -230,23 +272,45 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     }
 }
 
+// finest-level smoothing, bracketed by profiling events while recording the graph
 template <typename T>
-void cycle(mg_ctx* H, int l, cudaStream_t s) {
+void smooth_timed(mg_ctx* H, int l, int steps, cudaStream_t s) {
+    bool timed = H->recording && H->o.profile && l == H->L && steps > 0;
+    if (timed && H->pev_used + 2 <= (int)H->pev.size())
+        cudaEventRecordWithFlags(H->pev[H->pev_used], s, cudaEventRecordExternal);
+    smooth<T>(H, l, steps, s);
+    if (timed && H->pev_used + 2 <= (int)H->pev.size()) {
+        cudaEventRecordWithFlags(H->pev[H->pev_used + 1], s, cudaEventRecordExternal);
+        H->pev_used += 2;
+        H->sweeps_per_iter += steps;
+    }
+}
+
+// `count` consecutive cycles on level l for the same right-hand side
+template <typename T>
+void cycle(mg_ctx* H, int l, int count, cudaStream_t s) {
     Lev& v = H->lev[l];
     const LevelP<T>& P = lp<T>(v);
-    if (l == 1) {
-        launch_coarsest<T>(H->ainv, (const T*)v.f, (T*)v.x, P.fs, s);
+    if (l <= H->lc) {
+        launch_coarse_cycle<T>(ctap<T>(H), (const T*)v.f, (T*)v.x, H->ainv, count, s);
         H->rec_kernels += 1;
         return;
     }
-    Lev& c = H->lev[l - 1];
-    smooth<T>(H, l, H->o.nu_pre, s);
-    launch_restrict<T>(P, lp<T>(c), (const T*)v.f, (const T*)v.x, (T*)c.f, (T*)c.x, s);
-    H->rec_kernels += 1;
-    for (int g = 0; g < H->o.cycle; ++g) cycle<T>(H, l - 1, s);
-    launch_prolong<T>(P, lp<T>(c), (const T*)c.x, (T*)v.x, s);
-    H->rec_kernels += 1;
-    smooth<T>(H, l, H->o.nu_post, s);
+    for (int k = 0; k < count; ++k) {
+        if (l == 1) {
+            launch_coarsest<T>(H->ainv, (const T*)v.f, (T*)v.x, P.fs, s);
+            H->rec_kernels += 1;
+            continue;
+        }
+        Lev& c = H->lev[l - 1];
+        smooth_timed<T>(H, l, H->o.nu_pre, s);
+        launch_restrict<T>(P, lp<T>(c), (const T*)v.f, (const T*)v.x, (T*)c.f, (T*)c.x, s);
+        H->rec_kernels += 1;
+        cycle<T>(H, l - 1, H->o.cycle, s);
+        launch_prolong<T>(P, lp<T>(c), (const T*)c.x, (T*)v.x, s);
+        H->rec_kernels += 1;
+        smooth_timed<T>(H, l, H->o.nu_post, s);
+    }
 }
 
 // One iteration body (without the residual/norm launch):
@@ -256,10 +320,10 @@ void cycle(mg_ctx* H, int l, cudaStream_t s) {
 int record_iteration(mg_ctx* H, cudaStream_t s) {
     Lev& v = H->lev[H->L];
     if (!H->fp32) {
-        cycle<double>(H, H->L, s);
+        cycle<double>(H, H->L, 1, s);
     } else {
         CK(cudaMemsetAsync(v.x, 0, sizeof(float) * 2 * v.fs, s));
-        for (int c = 0; c < H->o.inner_cycles; ++c) cycle<float>(H, H->L, s);
+        cycle<float>(H, H->L, H->o.inner_cycles, s);
         launch_refine_update(H->fine64, H->x64, (const float*)v.x, v.ld, v.fs, s);
         H->rec_kernels += 1;
     }
@@ -268,9 +332,18 @@ int record_iteration(mg_ctx* H, cudaStream_t s) {
 
 int build_graph(mg_ctx* H) {
     CK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+    if (H->o.profile) {
+        int pairs = 2 * (H->fp32 ? H->o.inner_cycles : 1);
+        H->pev.resize(2 * pairs);
+        for (auto& e : H->pev) CK(cudaEventCreate(&e));
+    }
     CK(cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal));
     H->rec_kernels = 0;
+    H->recording = true;
+    H->pev_used = 0;
+    H->sweeps_per_iter = 0;
     int rc = record_iteration(H, H->cap);
+    H->recording = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(H->cap, &g);
     if (rc != AAOMG_OK) return rc;
@@ -284,6 +357,20 @@ int build_graph(mg_ctx* H) {
 double* iter_x(mg_ctx* H) { return H->fp32 ? H->x64 : (double*)H->lev[H->L].x; }
 double* iter_f(mg_ctx* H) { return H->fp32 ? H->f64 : (double*)H->lev[H->L].f; }
 
+// fold the event timings of the last graph launch into the profile (the
+// stream has been synchronised since that launch)
+int collect_profile(mg_ctx* H) {
+    if (!H->pending) return AAOMG_OK;
+    H->pending = false;
+    for (int p = 0; p + 1 < H->pev_used; p += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, H->pev[p], H->pev[p + 1]));
+        H->prof_ms += ms;
+    }
+    H->prof_sweeps += H->sweeps_per_iter;
+    return AAOMG_OK;
+}
+
 // residual of the FP64 iterate; in FP32 mode also writes the scaled FP32 defect
 // into the inner finest right-hand side.  Leaves norms in H->h_red after sync.
 int residual_norms(mg_ctx* H, cudaStream_t s, bool write_inner) {
@@ -294,12 +381,13 @@ int residual_norms(mg_ctx* H, cudaStream_t s, bool write_inner) {
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(H->h_red, H->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return AAOMG_OK;
+    return collect_profile(H);
 }
 
 int run_iteration(mg_ctx* H, cudaStream_t s) {
     CK(cudaGraphLaunch(H->gexec, s));
     H->launches += H->graph_kernels;
+    if (H->o.profile) H->pending = true;
     return AAOMG_OK;
 }
 
@@ -439,6 +527,20 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     if (rc) {
         mg_destroy(H);
         return rc;
+    }
+    {
+        int cap = H->fp32 ? max_cta_level<float>() : max_cta_level<double>();
+        int want = o.coarse_level < 0 ? cap : (o.coarse_level < cap ? o.coarse_level : cap);
+        H->lc = want < levels ? want : levels;
+        if (H->lc > 0) {
+            cudaError_t e = H->fp32 ? coarse_prepare<float>() : coarse_prepare<double>();
+            if (e != cudaSuccess) {
+                mg_destroy(H);
+                return fail(AAOMG_ERR_CUDA, std::string("coarse kernel attributes: ") + cudaGetErrorString(e));
+            }
+            if (H->fp32) H->cf = make_cta<float>(H, H->lc, true, km);
+            else H->cd = make_cta<double>(H, H->lc, false, km);
+        }
     }
     double inv[18 * 18];
     if (!coarse_inverse(alpha, H->fp32, km, inv)) {
@@ -631,6 +733,26 @@ int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol,
     CK(cudaMemcpyAsync(x_host, iter_x(h), bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return status;
+}
+
+int mg_get_profile(mg_handle h, double* smooth_ms, long long* sweeps) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    if ((rc = collect_profile(h))) return rc;
+    if (smooth_ms) *smooth_ms = h->prof_ms;
+    if (sweeps) *sweeps = h->prof_sweeps;
+    return AAOMG_OK;
+}
+
+int mg_reset_profile(mg_handle h) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    h->pending = false;
+    h->prof_ms = 0.0;
+    h->prof_sweeps = 0;
+    return AAOMG_OK;
 }
 
 int mg_get_history(mg_handle h, double* buf, int cap, int* n) {

@@ -37,7 +37,7 @@ AAOMG_HD constexpr int DJ(int o) { return (o == 3 || o == 5) ? 1 : ((o == 4 || o
 // Multicolour order of the LSGS sweep: colour(i,j) = (i + 2 j) mod 7 (a
 // distance-2 colouring: equal colours never share a neighbour), visited field
 // by field (y, then lambda) in the colour sequence 0,6,5,4,3,2,1.
-constexpr int kColourSeq[7] = {0, 6, 5, 4, 3, 2, 1};
+AAOMG_HD constexpr int colour_seq(int s) { return s == 0 ? 0 : 7 - s; }
 
 template <typename T>
 struct LevelP {
@@ -45,8 +45,9 @@ struct LevelP {
     int ld;      // row stride in elements
     int64_t fs;  // distance in elements between the y field and the lambda field
     T h2, c, d, invd, beta, km, tau;
-    // all-interior node (both the node and its neighbours off the boundary)
-    T mC, mO, kC, kE, kD;
+    // interior node: mass stencil mC (centre), mO (six neighbours); the bare
+    // stiffness stencil is 4 at the centre and -1 at E, W, N, S
+    T mC, mO;
     T invLy_int, invNy_int, invNl_int;
     // boundary classes: node class cls3(i)+3*cls3(j) (9) and cls5(i)+5*cls5(j) (25)
     T invLy[9];
@@ -69,10 +70,14 @@ AAOMG_HD void tri_counts(int i, int j, int n, int cnt[7]) {
     cnt[0] = 2 * ip * jp + im * jp + ip * jm + 2 * im * jm;
 }
 
-// A-row coefficients of node (i,j): M_o and K_o for the 7 offsets (zero for
-// offsets that leave the domain).
+// A-row coefficients of node (i,j) for the 7 offsets (zero for offsets that
+// leave the domain): the mass stencil m and the bare stiffness stencil kd.
+// K = kd + km m is never formed coefficient-wise: the mass part of K is about
+// h^2/8 of its diagonal, below FP32 resolution on fine grids, so every kernel
+// applies K v as (kd . v) + km (m . v).  The stiffness sum cancels exactly for
+// smooth v (neighbouring values are close), which keeps the O(h^2) mass term.
 template <typename T>
-AAOMG_HD void row_coeffs_general(int i, int j, int n, T h2, T km, T m[7], T k[7]) {
+AAOMG_HD void row_coeffs_general(int i, int j, int n, T h2, T m[7], T kd[7]) {
     int cnt[7];
     tri_counts(i, j, n, cnt);
     const T q = h2 / T(24);
@@ -80,11 +85,10 @@ AAOMG_HD void row_coeffs_general(int i, int j, int n, T h2, T km, T m[7], T k[7]
     T kd0 = T(0);
     for (int o = 1; o < 7; ++o) {
         m[o] = T(cnt[o]) * q;
-        T kd = (o <= 4) ? T(-0.5) * T(cnt[o]) : T(0);
-        kd0 -= kd;
-        k[o] = kd + km * m[o];
+        kd[o] = (o <= 4) ? T(-0.5) * T(cnt[o]) : T(0);
+        kd0 -= kd[o];
     }
-    k[0] = kd0 + km * m[0];
+    kd[0] = kd0;
 }
 
 AAOMG_HD bool in_grid(int i, int j, int n) { return i >= 0 && i <= n && j >= 0 && j <= n; }

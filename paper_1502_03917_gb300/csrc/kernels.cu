@@ -6,87 +6,11 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "stencil.cuh"
 
 namespace aaomg {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ bool node_interior(const LevelP<T>& P, int i, int j) {
-    return i > 0 && i < P.n && j > 0 && j < P.n;
-}
-
-template <typename T>
-__device__ __forceinline__ void row_coeffs(const LevelP<T>& P, int i, int j, T m[7], T k[7]) {
-    if (node_interior(P, i, j)) {
-        m[0] = P.mC;
-        k[0] = P.kC;
-#pragma unroll
-        for (int o = 1; o < 7; ++o) {
-            m[o] = P.mO;
-            k[o] = o <= 4 ? P.kE : P.kD;
-        }
-    } else {
-        row_coeffs_general<T>(i, j, P.n, P.h2, P.km, m, k);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ T inv_ly(const LevelP<T>& P, int i, int j) {
-    return node_interior(P, i, j) ? P.invLy_int : P.invLy[cls3(i, P.n) + 3 * cls3(j, P.n)];
-}
-
-template <typename T>
-__device__ __forceinline__ bool all_interior(const LevelP<T>& P, int i, int j) {
-    return i >= 2 && i <= P.n - 2 && j >= 2 && j <= P.n - 2;
-}
-
-template <typename T>
-__device__ __forceinline__ T inv_n(const LevelP<T>& P, int field, int i, int j) {
-    if (all_interior(P, i, j)) return field == 0 ? P.invNy_int : P.invNl_int;
-    int c = cls5(i, P.n) + 5 * cls5(j, P.n);
-    return field == 0 ? P.invNy[c] : P.invNl[c];
-}
-
-// v at the 7 offsets of node (i,j); 0 where the offset leaves the grid
-template <typename T>
-__device__ __forceinline__ void load7(const LevelP<T>& P, const T* __restrict__ v, int i, int j, T out[7]) {
-    if (node_interior(P, i, j)) {
-        const T* p = v + (int64_t)j * P.ld + i;
-#pragma unroll
-        for (int o = 0; o < 7; ++o) out[o] = p[DJ(o) * P.ld + DI(o)];
-    } else {
-#pragma unroll
-        for (int o = 0; o < 7; ++o) {
-            int ii = i + DI(o), jj = j + DJ(o);
-            out[o] = in_grid(ii, jj, P.n) ? v[(int64_t)jj * P.ld + ii] : T(0);
-        }
-    }
-}
-
-// (A x) at node (i,j): returns ay = (M y + c K lambda), al = (c K y - d M lambda)
-template <typename T>
-__device__ __forceinline__ void apply_A(const LevelP<T>& P, const T* x, int i, int j, T& ay, T& al) {
-    T m[7], k[7], y[7], l[7];
-    row_coeffs(P, i, j, m, k);
-    load7(P, x, i, j, y);
-    load7(P, x + P.fs, i, j, l);
-    T My = 0, Kl = 0, Ky = 0, Ml = 0;
-#pragma unroll
-    for (int o = 0; o < 7; ++o) {
-        My += m[o] * y[o];
-        Kl += k[o] * l[o];
-        Ky += k[o] * y[o];
-        Ml += m[o] * l[o];
-    }
-    ay = My + P.c * Kl;
-    al = P.c * Ky - P.d * Ml;
-}
-
-template <typename T>
-__device__ __forceinline__ int64_t nidx(const LevelP<T>& P, int i, int j) {
-    return (int64_t)j * P.ld + i;
-}
 
 // ---------------------------------------------------------------- kernels --
 
@@ -96,12 +20,7 @@ __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __res
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > P.n || j > P.n) return;
-    T ay, al;
-    apply_A(P, x, i, j, ay, al);
-    int64_t p = nidx(P, i, j);
-    T il = inv_ly(P, i, j);
-    rh[p] = (f[p] - ay) * il;
-    rh[p + P.fs] = (f[p + P.fs] - al) * (il * P.invd);
+    resid_hat_at(P, f, x, rh, i, j);
 }
 
 // Algorithm 1 update: x += tau L^{-1} A rh (A symmetric), with rh = L^{-1} r
@@ -110,12 +29,7 @@ __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict_
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > P.n || j > P.n) return;
-    T qy, ql;
-    apply_A(P, rh, i, j, qy, ql);
-    int64_t p = nidx(P, i, j);
-    T il = inv_ly(P, i, j);
-    x[p] += P.tau * il * qy;
-    x[p + P.fs] += P.tau * (il * P.invd) * ql;
+    ne_update_at(P, x, rh, i, j);
 }
 
 // One colour phase of Algorithm 2: every unknown of field `field` on a node of
@@ -128,34 +42,7 @@ __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__
     if (j > P.n) return;
     int i = ((colour - 2 * j) % 7 + 7) % 7 + 7 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i > P.n) return;
-    T m[7], k[7], ry[7], rl[7];
-    row_coeffs(P, i, j, m, k);
-    load7(P, rh, i, j, ry);
-    load7(P, rh + P.fs, i, j, rl);
-    T q = 0;
-    if (field == 0) {
-#pragma unroll
-        for (int o = 0; o < 7; ++o) q += m[o] * ry[o] + P.c * k[o] * rl[o];
-    } else {
-#pragma unroll
-        for (int o = 0; o < 7; ++o) q += P.c * k[o] * ry[o] - P.d * m[o] * rl[o];
-    }
-    T p = q * inv_n(P, field, i, j);
-    x[nidx(P, i, j) + (field ? P.fs : 0)] += p;
-#pragma unroll
-    for (int o = 0; o < 7; ++o) {
-        int ii = i + DI(o), jj = j + DJ(o);
-        if (!in_grid(ii, jj, P.n)) continue;
-        T il = inv_ly(P, ii, jj);
-        int64_t q2 = nidx(P, ii, jj);
-        if (field == 0) {
-            rh[q2] = ry[o] - m[o] * p * il;
-            rh[q2 + P.fs] = rl[o] - P.c * k[o] * p * (il * P.invd);
-        } else {
-            rh[q2] = ry[o] - P.c * k[o] * p * il;
-            rh[q2 + P.fs] = rl[o] + m[o] * p * il;
-        }
-    }
+    lsgs_update_at(P, field, x, rh, i, j);
 }
 
 // Defect restriction: fc = P^T (f - A x) on a coarse node (I,J) -- weight 1 at
@@ -167,18 +54,8 @@ __global__ void k_restrict(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ f, 
     int I = blockIdx.x * blockDim.x + threadIdx.x;
     int J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I > Pc.n || J > Pc.n) return;
-    T sy = 0, sl = 0;
-#pragma unroll
-    for (int o = 0; o < 7; ++o) {
-        int i = 2 * I + DI(o), j = 2 * J + DJ(o);
-        if (!in_grid(i, j, Pf.n)) continue;
-        T ay, al;
-        apply_A(Pf, x, i, j, ay, al);
-        int64_t p = nidx(Pf, i, j);
-        T w = o == 0 ? T(1) : T(0.5);
-        sy += w * (f[p] - ay);
-        sl += w * (f[p + Pf.fs] - al);
-    }
+    T sy, sl;
+    restrict_at(Pf, f, x, I, J, sy, sl);
     int64_t c = nidx(Pc, I, J);
     fc[c] = sy;
     fc[c + Pc.fs] = sl;
@@ -192,20 +69,11 @@ __global__ void k_prolong(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ xc, 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > Pf.n || j > Pf.n) return;
-    int I = i >> 1, J = j >> 1;
-    int64_t a = nidx(Pc, I, J);
-    int64_t b = a;
-    if ((i & 1) && (j & 1)) b = nidx(Pc, I + 1, J + 1);
-    else if (i & 1) b = nidx(Pc, I + 1, J);
-    else if (j & 1) b = nidx(Pc, I, J + 1);
+    T vy, vl;
+    prolong_at(Pf, Pc, xc, i, j, vy, vl);
     int64_t p = nidx(Pf, i, j);
-    if (a == b) {
-        x[p] += xc[a];
-        x[p + Pf.fs] += xc[a + Pc.fs];
-    } else {
-        x[p] += T(0.5) * (xc[a] + xc[b]);
-        x[p + Pf.fs] += T(0.5) * (xc[a + Pc.fs] + xc[b + Pc.fs]);
-    }
+    x[p] += vy;
+    x[p + Pf.fs] += vl;
 }
 
 // exact solve on the coarsest grid (18 unknowns): x = A_1^{-1} f in FP64
@@ -337,8 +205,8 @@ __global__ void k_rhs(LevelP<double> P, const double* __restrict__ yD, double* _
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > P.n || j > P.n) return;
-    double m[7], k[7], y[7];
-    row_coeffs(P, i, j, m, k);
+    double m[7], kd[7], y[7];
+    row_coeffs(P, i, j, m, kd);
     // yD is packed with stride n+1
     LevelP<double> Q = P;
     Q.ld = P.n + 1;
