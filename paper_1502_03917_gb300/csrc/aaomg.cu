@@ -171,7 +171,10 @@ struct mg_ctx {
     int dev = 0;
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
-    int lc = 0;               // levels <= lc run inside the single-block coarse kernel
+    int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
+    int ld = 0;               // level whose gamma coarse-grid steps are one dense map (0: none)
+    void* bdense = nullptr;   // that map, (2 N_ld)^2 in the cycle's precision, row-major
+    int bm = 0;
     CtaParams<float> cf{};
     CtaParams<double> cd{};
     LevelP<double> fine64{};  // the paper's system on the finest level, user layout
@@ -296,6 +299,13 @@ void cycle(mg_ctx* H, int l, int count, cudaStream_t s) {
         H->rec_kernels += 1;
         return;
     }
+    if (l == H->ld && count == H->o.cycle) {
+        // the gamma cycles from the zero initial guess set by the restriction:
+        // x = Bd f with the precomputed dense map
+        launch_dense_apply<T>((const T*)H->bdense, H->bm, (const T*)v.f, (T*)v.x, s);
+        H->rec_kernels += 1;
+        return;
+    }
     for (int k = 0; k < count; ++k) {
         if (l == 1) {
             launch_coarsest<T>(H->ainv, (const T*)v.f, (T*)v.x, P.fs, s);
@@ -328,6 +338,40 @@ int record_iteration(mg_ctx* H, cudaStream_t s) {
         H->rec_kernels += 1;
     }
     return AAOMG_OK;
+}
+
+// Dense map of the gamma coarse-grid steps on level ld (from a zero initial
+// guess, the steps are linear in the right-hand side): computed column by column
+// in FP64 by the single-block kernel, one block per unit vector, with the
+// operator scaled as the cycles use it; stored in the cycles' precision.
+int build_dense_coarse(mg_ctx* H, double km) {
+    int ld = H->ld;
+    int64_t m = 2 * (int64_t)((1 << ld) + 1) * ((1 << ld) + 1);
+    H->bm = (int)m;
+    double* tmp = nullptr;
+    double* ainv64 = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * m * m));
+    CK(cudaMalloc(&ainv64, sizeof(double) * 18 * 18));
+    double inv[18 * 18];
+    coarse_inverse(H->alpha, H->fp32, km, inv);
+    CK(cudaMemcpy(ainv64, inv, sizeof(inv), cudaMemcpyHostToDevice));
+    CtaParams<double> C = make_cta<double>(H, ld, H->fp32, km);
+    cudaError_t e = launch_coarse_basis<double>(C, ainv64, H->o.cycle, tmp, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int rc = AAOMG_OK;
+    if (e != cudaSuccess) rc = fail(AAOMG_ERR_CUDA, std::string("dense coarse map: ") + cudaGetErrorString(e));
+    if (!rc) {
+        size_t es = H->fp32 ? sizeof(float) : sizeof(double);
+        if ((rc = dalloc(H, &H->bdense, es * m * m)) == AAOMG_OK) {
+            if (H->fp32) launch_f64_to_f32(tmp, (float*)H->bdense, m * m, 0);
+            else e = cudaMemcpy(H->bdense, tmp, sizeof(double) * m * m, cudaMemcpyDeviceToDevice);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) rc = fail(AAOMG_ERR_CUDA, std::string("dense coarse map: ") + cudaGetErrorString(e));
+        }
+    }
+    cudaFree(tmp);
+    cudaFree(ainv64);
+    return rc;
 }
 
 int build_graph(mg_ctx* H) {
@@ -528,11 +572,16 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         mg_destroy(H);
         return rc;
     }
-    {
-        int cap = H->fp32 ? max_cta_level<float>() : max_cta_level<double>();
-        int want = o.coarse_level < 0 ? cap : (o.coarse_level < cap ? o.coarse_level : cap);
-        H->lc = want < levels ? want : levels;
-        if (H->lc > 0) {
+    // Coarse end of the cycle: with coarse_level d (default 5), a problem with
+    // levels <= d runs whole cycles in the single-block kernel; a larger one
+    // replaces the gamma coarse-grid steps on level d by a dense map computed
+    // here.  coarse_level 0 keeps grid-wide kernels on every level.
+    int dcoarse = 0;
+    if (o.coarse_level != 0) {
+        int cap = max_cta_level<double>();
+        dcoarse = o.coarse_level < 0 ? 5 : (o.coarse_level < cap ? o.coarse_level : cap);
+        if (levels <= dcoarse) {
+            H->lc = levels;
             cudaError_t e = H->fp32 ? coarse_prepare<float>() : coarse_prepare<double>();
             if (e != cudaSuccess) {
                 mg_destroy(H);
@@ -540,6 +589,8 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
             }
             if (H->fp32) H->cf = make_cta<float>(H, H->lc, true, km);
             else H->cd = make_cta<double>(H, H->lc, false, km);
+        } else if (dcoarse >= 2) {
+            H->ld = dcoarse;
         }
     }
     double inv[18 * 18];
@@ -566,6 +617,10 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     if (e != cudaSuccess) {
         mg_destroy(H);
         return fail(AAOMG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (H->ld > 0 && (rc = build_dense_coarse(H, km))) {
+        mg_destroy(H);
+        return rc;
     }
     if ((rc = build_graph(H))) {
         mg_destroy(H);

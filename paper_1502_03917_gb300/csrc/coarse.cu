@@ -85,42 +85,66 @@ __device__ void cta_coarsest(const CtaState<T>& S) {
 }
 
 template <typename T>
-__device__ void cta_cycle(const CtaParams<T>& C, const CtaState<T>& S, int l) {
-    if (l == 1) {
-        cta_coarsest(S);
-        return;
-    }
+__device__ void cta_restrict(const CtaParams<T>& C, const CtaState<T>& S, int l) {
     const LevelP<T>& P = C.P[l];
     const LevelP<T>& Pc = C.P[l - 1];
-    cta_smooth(C, S, l, C.nu_pre);
-    {
-        const int nc1 = Pc.n + 1;
-        for (int t = threadIdx.x; t < nc1 * nc1; t += blockDim.x) {
-            int I = t % nc1, J = t / nc1;
-            T sy, sl;
-            restrict_at(P, S.f[l], S.x[l], I, J, sy, sl);
-            int64_t c = nidx(Pc, I, J);
-            S.f[l - 1][c] = sy;
-            S.f[l - 1][c + Pc.fs] = sl;
-            S.x[l - 1][c] = T(0);
-            S.x[l - 1][c + Pc.fs] = T(0);
-        }
-        __syncthreads();
+    const int nc1 = Pc.n + 1;
+    for (int t = threadIdx.x; t < nc1 * nc1; t += blockDim.x) {
+        int I = t % nc1, J = t / nc1;
+        T sy, sl;
+        restrict_at(P, S.f[l], S.x[l], I, J, sy, sl);
+        int64_t c = nidx(Pc, I, J);
+        S.f[l - 1][c] = sy;
+        S.f[l - 1][c + Pc.fs] = sl;
+        S.x[l - 1][c] = T(0);
+        S.x[l - 1][c + Pc.fs] = T(0);
     }
-    for (int g = 0; g < C.gamma; ++g) cta_cycle(C, S, l - 1);
-    {
-        const int n1 = P.n + 1;
-        for (int t = threadIdx.x; t < n1 * n1; t += blockDim.x) {
-            int i = t % n1, j = t / n1;
-            T vy, vl;
-            prolong_at(P, Pc, S.x[l - 1], i, j, vy, vl);
-            int64_t p = nidx(P, i, j);
-            S.x[l][p] += vy;
-            S.x[l][p + P.fs] += vl;
-        }
-        __syncthreads();
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void cta_prolong(const CtaParams<T>& C, const CtaState<T>& S, int l) {
+    const LevelP<T>& P = C.P[l];
+    const LevelP<T>& Pc = C.P[l - 1];
+    const int n1 = P.n + 1;
+    for (int t = threadIdx.x; t < n1 * n1; t += blockDim.x) {
+        int i = t % n1, j = t / n1;
+        T vy, vl;
+        prolong_at(P, Pc, S.x[l - 1], i, j, vy, vl);
+        int64_t p = nidx(P, i, j);
+        S.x[l][p] += vy;
+        S.x[l][p + P.fs] += vl;
     }
-    cta_smooth(C, S, l, C.nu_post);
+    __syncthreads();
+}
+
+// `ncycles` cycles on level `top`, each recursing gamma times per level (the
+// recursion of section 2 unrolled into a loop with one counter per level, so
+// that the stack size is static).
+template <typename T>
+__device__ void cta_cycles(const CtaParams<T>& C, const CtaState<T>& S, int top, int ncycles) {
+    int todo[kMaxCtaLevel + 2];
+    todo[top + 1] = ncycles;
+    int l = top;
+    for (;;) {
+        // start a cycle on level l: pre-smooth and restrict down to level 1
+        while (l > 1) {
+            cta_smooth(C, S, l, C.nu_pre);
+            cta_restrict(C, S, l);
+            todo[l] = C.gamma;
+            --l;
+        }
+        cta_coarsest(S);
+        // the cycle on level l is complete; climb while parents are complete
+        for (;;) {
+            int parent = l + 1;
+            if (--todo[parent] > 0) break;  // another cycle on level l
+            if (parent > top) return;
+            cta_prolong(C, S, parent);
+            cta_smooth(C, S, parent, C.nu_post);
+            l = parent;
+        }
+    }
 }
 
 template <typename T>
@@ -151,13 +175,43 @@ __global__ void __launch_bounds__(cta_threads<T>()) k_coarse_cycle(CtaParams<T> 
         S.x[C.lc][q + P.fs] = xg[g + C.g_fs];
     }
     __syncthreads();
-    for (int c = 0; c < ncycles; ++c) cta_cycle(C, S, C.lc);
+    cta_cycles(C, S, C.lc, ncycles);
     for (int t = threadIdx.x; t < n1 * n1; t += blockDim.x) {
         int i = t % n1, j = t / n1;
         int64_t g = (int64_t)j * C.g_ld + i, q = nidx(P, i, j);
         xg[g] = S.x[C.lc][q];
         xg[g + C.g_fs] = S.x[C.lc][q + P.fs];
     }
+}
+
+// Columns of the dense operator of `ncycles` cycles from a zero initial guess
+// on level lc: block k runs the cycles with f = e_k and stores the result as
+// column k of Bd (row-major m x m, m = 2 (n+1)^2), in FP64.
+template <typename T>
+__global__ void __launch_bounds__(cta_threads<T>()) k_coarse_basis(CtaParams<T> C, const double* __restrict__ ainv,
+                                                                   int ncycles, double* __restrict__ Bd) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    CtaState<T> S;
+    double* a = reinterpret_cast<double*>(smem);
+    T* p = reinterpret_cast<T*>(smem + 18 * 18 * sizeof(double));
+    for (int l = 1; l <= C.lc; ++l) {
+        int64_t sz = 2 * C.P[l].fs;
+        S.x[l] = p;
+        S.f[l] = p + sz;
+        S.rh[l] = p + 2 * sz;
+        p += 3 * sz;
+    }
+    S.ainv = a;
+    for (int t = threadIdx.x; t < 18 * 18; t += blockDim.x) a[t] = ainv[t];
+    const int64_t m = 2 * C.P[C.lc].fs;
+    const int k = blockIdx.x;
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+        S.f[C.lc][t] = T(t == k ? 1 : 0);
+        S.x[C.lc][t] = T(0);
+    }
+    __syncthreads();
+    cta_cycles(C, S, C.lc, ncycles);
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) Bd[t * m + k] = (double)S.x[C.lc][t];
 }
 
 }  // namespace
@@ -183,6 +237,17 @@ void launch_coarse_cycle(const CtaParams<T>& C, const T* f, T* x, const double* 
     k_coarse_cycle<T><<<1, cta_threads<T>(), coarse_smem_bytes<T>(C.lc), s>>>(C, f, x, ainv, ncycles);
 }
 
+template <typename T>
+cudaError_t launch_coarse_basis(const CtaParams<T>& C, const double* ainv, int ncycles, double* Bd, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_basis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)coarse_smem_bytes<T>(max_cta_level<T>()));
+    if (e != cudaSuccess) return e;
+    int m = (int)(2 * C.P[C.lc].fs);
+    k_coarse_basis<T><<<m, cta_threads<T>(), coarse_smem_bytes<T>(C.lc), s>>>(C, ainv, ncycles, Bd);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_coarse_basis<double>(const CtaParams<double>&, const double*, int, double*, cudaStream_t);
 template size_t coarse_smem_bytes<float>(int);
 template size_t coarse_smem_bytes<double>(int);
 template cudaError_t coarse_prepare<float>();

@@ -27,6 +27,16 @@ template <typename T>
 size_t coarse_smem_bytes(int lc);
 template <typename T>
 cudaError_t coarse_prepare();
+// FP64 columns of the dense map "ncycles cycles from zero on level C.lc"
+// (row-major, m x m with m = 2 (2^lc+1)^2)
+template <typename T>
+cudaError_t launch_coarse_basis(const CtaParams<T>& C, const double* ainv, int ncycles, double* Bd, cudaStream_t s);
+
+// x = B f for a dense row-major m x m operator (one warp per row)
+template <typename T>
+void launch_dense_apply(const T* B, int m, const T* f, T* x, cudaStream_t s);
+void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+
 template <typename T>
 void launch_coarse_cycle(const CtaParams<T>& C, const T* f, T* x, const double* ainv, int ncycles, cudaStream_t s);
 

@@ -4,6 +4,7 @@
 // applied matrix-free from the coefficients of common.cuh.
 #include <cuda_runtime.h>
 
+#include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
 #include "stencil.cuh"
@@ -281,5 +282,48 @@ void launch_rhs(const LevelP<double>& P, const double* yD, double* f, cudaStream
     template void launch_coarsest<T>(const double*, const T*, T*, int64_t, cudaStream_t);
 AAOMG_INST(float)
 AAOMG_INST(double)
+
+}  // namespace aaomg
+
+// ------------------------------------------------------ dense coarse map --
+namespace aaomg {
+namespace {
+
+// x = B f, B dense row-major m x m: one warp per output row, f staged in
+// shared memory; the row sum is reduced in a fixed lane order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply(const T* __restrict__ B, int m, const T* __restrict__ f,
+                                                     T* __restrict__ x) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* fs = reinterpret_cast<T*>(smem_raw);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) fs[t] = f[t];
+    __syncthreads();
+    int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (r >= m) return;
+    const T* row = B + (int64_t)r * m;
+    T s = T(0);
+    for (int k = lane; k < m; k += 32) s += row[k] * fs[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] = s;
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (float)a[t];
+}
+
+}  // namespace
+
+template <typename T>
+void launch_dense_apply(const T* B, int m, const T* f, T* x, cudaStream_t s) {
+    k_dense_apply<T><<<(m + 7) / 8, 256, m * sizeof(T), s>>>(B, m, f, x);
+}
+void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+    k_f64_to_f32<<<1024, 256, 0, s>>>(a, b, n);
+}
+template void launch_dense_apply<float>(const float*, int, const float*, float*, cudaStream_t);
+template void launch_dense_apply<double>(const double*, int, const double*, double*, cudaStream_t);
 
 }  // namespace aaomg
