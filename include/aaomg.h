@@ -88,6 +88,8 @@ typedef struct mg_options {
     int inner_cycles; /* FP32_REFINE: FP32 cycles per refinement step; <= 0: 3 */
     int coarse_level; /* levels <= this run inside one single-block kernel; < 0: default, 0: none */
     int profile;      /* 1: time the finest-level smoothing inside every iteration (CUDA events) */
+    int tile_w;       /* LSGS step kernel: owned columns per block; <= 0: widest the block allows */
+    int tile_h;       /* LSGS step kernel: owned rows per block; <= 0: chosen to fill the GPU */
 } mg_options;
 
 /* Build the hierarchy for h = 2^-levels (1 <= levels <= 13; level 1 is the

@@ -5,9 +5,9 @@ Workload: Poisson control on the unit square at h = 2^-11 (2049 x 2049 nodes,
 8.4M unknowns), y_D = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1) (seed 1), W-cycle
 with 2+2 smoothing steps down to h = 1/2, for alpha in {1, 1e-2, 1e-4, 1e-6,
 1e-8} and the NE and LSGS smoothers.  Each solve runs to a relative residual of
-1e-12; the file keeps the residual history (so the iteration count to any
-tolerance above 1e-12 can be read off), and the solution at 256 seeded node
-indices.
+1e-10 (at this size FP64 rounding stalls the residual near 3e-11 for alpha = 1);
+the file keeps the residual history (so the iteration count to any tolerance
+above 1e-10 can be read off), and the solution at 256 seeded node indices.
 
 Usage: python oracle/make_golden.py [L]   (takes tens of minutes on one core)
 """
@@ -40,9 +40,9 @@ def main():
             t0 = time.time()
             o = oracle.Oracle(L, a, smoother=smoother)
             f = o.rhs(yD)
-            x, it, rr, hist = o.solve(f, tol=1e-12, max_iter=120)
+            x, it, rr, hist = o.solve(f, tol=1e-10, max_iter=60)
             res["runs"].append({
-                "smoother": smoother, "alpha": a, "iterations_to_1e-12": it, "relres": rr,
+                "smoother": smoother, "alpha": a, "iterations_to_1e-10": it, "relres": rr,
                 "history": hist.tolist(),
                 "y": x[sample].tolist(), "lambda": x[nn + sample].tolist(),
                 "seconds": time.time() - t0,

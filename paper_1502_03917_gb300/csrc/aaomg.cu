@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "aaomg.h"
+#include "band.h"
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
@@ -37,8 +38,10 @@ struct Lev {
     int n = 0, ld = 0;
     int64_t fs = 0;
     void* x = nullptr;
+    void* x2 = nullptr;  // second iterate buffer for the out-of-place LSGS step
     void* f = nullptr;
     void* rh = nullptr;
+    BandGrid bg{};
     LevelP<float> pf{};
     LevelP<double> pd{};
 };
@@ -169,6 +172,7 @@ struct mg_ctx {
     double alpha = 0.0, beta = 0.0;
     mg_options o{};
     int dev = 0;
+    int nsm = 152;
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -258,6 +262,22 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
             H->rec_kernels += 2;
         }
         break;
+    case MG_SMOOTHER_LSGS: {
+        // one launch per step, ping-pong between x and x2
+        T* a = x;
+        T* b = (T*)v.x2;
+        for (int m = 0; m < steps; ++m) {
+            launch_lsgs_band<T>(P, f, a, b, v.bg, s);
+            T* t = a;
+            a = b;
+            b = t;
+        }
+        H->rec_kernels += steps;
+        if (a != x) {
+            cudaMemcpyAsync(x, a, sizeof(T) * 2 * v.fs, cudaMemcpyDeviceToDevice, s);
+        }
+        break;
+    }
     default: {
         launch_resid_hat<T>(P, f, x, rh, s);
         H->rec_kernels += 1;
@@ -548,7 +568,15 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     H->o = o;
     H->dev = dev;
     H->fp32 = o.precision == MG_PREC_FP32_REFINE;
+    H->nsm = prop.multiProcessorCount;
     const double km = o.k_variant == 0 ? 1.0 : 0.0;
+    {
+        cudaError_t e = H->fp32 ? band_prepare<float>() : band_prepare<double>();
+        if (e != cudaSuccess) {
+            delete H;
+            return fail(AAOMG_ERR_CUDA, std::string("band kernel attributes: ") + cudaGetErrorString(e));
+        }
+    }
     int rc = AAOMG_OK;
     {
         int n = 1 << levels;
@@ -561,8 +589,12 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         v.fs = (int64_t)v.ld * (v.n + 1);
         size_t es = H->fp32 ? sizeof(float) : sizeof(double);
         size_t bytes = es * 2 * (size_t)v.fs;
-        if ((rc = dalloc(H, &v.x, bytes)) || (rc = dalloc(H, &v.f, bytes)) || (rc = dalloc(H, &v.rh, bytes))) break;
+        if ((rc = dalloc(H, &v.x, bytes)) || (rc = dalloc(H, &v.x2, bytes)) || (rc = dalloc(H, &v.f, bytes)) ||
+            (rc = dalloc(H, &v.rh, bytes)))
+            break;
         CK(cudaMemset(v.x, 0, bytes));
+        CK(cudaMemset(v.x2, 0, bytes));
+        v.bg = H->fp32 ? band_grid<float>(v.n, o.tile_w, o.tile_h, H->nsm) : band_grid<double>(v.n, o.tile_w, o.tile_h, H->nsm);
         CK(cudaMemset(v.f, 0, bytes));
         CK(cudaMemset(v.rh, 0, bytes));
         v.pd = make_params<double>(v.n, v.ld, v.fs, alpha, false, km, o.tau);

@@ -45,7 +45,7 @@ def field_reldiff(a, b, n):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
-@pytest.mark.parametrize("L", [2, 3, 5, 7])
+@pytest.mark.parametrize("L", [2, 3, 5, 7, 9])
 @pytest.mark.parametrize("alpha", [1.0, 1e-4, 1e-8])
 def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
     x0 = inputs.f32_exact(inputs.x_uniform(L, 100 + L))
@@ -59,6 +59,25 @@ def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
             got = host(x)
             want = o.smooth(f, x0, steps)
             d = field_reldiff(got, want, n)
+            assert d <= TOL[precision], (steps, d)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("tile", [(0, 0), (20, 9), (1, 1), (57, 130), (3, 40)])
+@pytest.mark.parametrize("L", [2, 4, 8])
+def test_lsgs_step_kernel_tiling(mg, oracle_mod, L, tile, precision):
+    """The one-launch LSGS step (wavefront over bands of columns and segments
+    of rows, with recomputed halos) equals the sequential multicolour sweep for
+    every tiling, including one-node tiles and an odd number of steps."""
+    alpha = 1e-3
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 300 + L))
+    f = inputs.f32_exact(inputs.x_uniform(L, 400 + L))
+    o = oracle_mod.Oracle(L, alpha, smoother="lsgs")
+    with mg.Solver(L, alpha, smoother="lsgs", precision=precision, tile_w=tile[0], tile_h=tile[1]) as s:
+        for steps in (1, 3):
+            x = dev(x0)
+            s.smooth(dev(f), x, steps)
+            d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
             assert d <= TOL[precision], (steps, d)
 
 
