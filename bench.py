@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--serial", action="store_true",
+                   help="solve the alphas one after another instead of concurrently on separate streams")
     return p.parse_args()
 
 
@@ -145,16 +147,51 @@ def run_ours(args, rank, world, local):
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
+    streams = {a: torch.cuda.Stream() for a in ALPHAS}
+
+    def run_all(fn):
+        """fn(alpha) for every alpha: concurrently, one host thread and one CUDA
+        stream per alpha (independent problems), or one after another."""
+        if args.serial:
+            for a in ALPHAS:
+                fn(a)
+            return
+        main = torch.cuda.current_stream()
+        ready = torch.cuda.Event()
+        ready.record(main)
+        errs = []
+
+        def work(a):
+            try:
+                with torch.cuda.stream(streams[a]):
+                    streams[a].wait_event(ready)
+                    fn(a)
+            except BaseException as e:  # surfaced below
+                errs.append(e)
+
+        ts = [threading.Thread(target=work, args=(a,)) for a in ALPHAS]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        if errs:
+            raise errs[0]
+        for a in ALPHAS:
+            main.wait_stream(streams[a])
+
     def timed_steps(solvers, K, W):
         fs = {a: s.rhs_from_yd(yD) for a, s in solvers.items()}
         xs = {a: torch.zeros_like(fs[a]) for a in solvers}
         its = {}
+        torch.cuda.synchronize()
+
+        def one(a):
+            xs[a].zero_()
+            it, rr, code = solvers[a].solve(fs[a], xs[a], tol=args.tol)
+            its[a] = it
 
         def step():
-            for a, s in solvers.items():
-                xs[a].zero_()
-                it, rr, code = s.solve(fs[a], xs[a], tol=args.tol)
-                its[a] = it
+            run_all(one)
 
         for _ in range(W):
             step()
@@ -219,7 +256,8 @@ def run_ours(args, rank, world, local):
                                   f"refinement, tol {args.tol}",
                       "level": L, "unknowns_per_solve": 2 * N, "solves_per_step": len(ALPHAS),
                       "smoother": args.smoother, "cycle": args.cycle, "precision": "fp32_refine",
-                      "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+                      "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                      "concurrency": 1 if args.serial else len(ALPHAS)},
            "iterations": {str(a): its32[a] for a in ALPHAS},
            "roofline": roofline, "clocks": clocks, "gpu_launches": launches}
 
@@ -240,7 +278,7 @@ def run_ours(args, rank, world, local):
             s.close()
 
     if not args.no_e2e:
-        out["e2e"] = run_e2e(args, sol32, yD, K, world, max_over_ranks)
+        out["e2e"] = run_e2e(args, sol32, yD, K, world, max_over_ranks, run_all)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(L, args, its_gpu=out.get("fp64_plain", {}).get("iterations"))
@@ -252,7 +290,7 @@ def run_ours(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
-def run_e2e(args, solvers, yD, K, world, max_over_ranks):
+def run_e2e(args, solvers, yD, K, world, max_over_ranks, run_all):
     """Same metric through mg_solve_host: f and x in pinned host memory, the
     host-to-device and device-to-host copies inside the timed region."""
     import torch
@@ -264,13 +302,15 @@ def run_e2e(args, solvers, yD, K, world, max_over_ranks):
         hf = torch.empty(2 * N, dtype=torch.float64, pin_memory=True)
         hf.copy_(f)
         host_f[a] = hf
-    hx = torch.empty(2 * N, dtype=torch.float64, pin_memory=True)
+    hx = {a: torch.empty(2 * N, dtype=torch.float64, pin_memory=True) for a in solvers}
     torch.cuda.synchronize()
 
+    def one(a):
+        hx[a].zero_()
+        solvers[a].solve_host(host_f[a].numpy(), hx[a].numpy(), tol=args.tol)
+
     def step():
-        for a, s in solvers.items():
-            hx.zero_()
-            s.solve_host(host_f[a].numpy(), hx.numpy(), tol=args.tol)
+        run_all(one)
 
     step()  # warm-up
     torch.cuda.synchronize()

@@ -173,6 +173,7 @@ struct mg_ctx {
     mg_options o{};
     int dev = 0;
     int nsm = 152;
+    int band_min = 257;       // levels with at least this many nodes per side use the one-launch LSGS step
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -263,6 +264,7 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
         }
         break;
     case MG_SMOOTHER_LSGS: {
+        if (v.n + 1 < H->band_min) goto phases;
         // one launch per step, ping-pong between x and x2
         T* a = x;
         T* b = (T*)v.x2;
@@ -278,7 +280,8 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
         }
         break;
     }
-    default: {
+    default:
+    phases: {
         launch_resid_hat<T>(P, f, x, rh, s);
         H->rec_kernels += 1;
         for (int m = 0; m < steps; ++m) {
@@ -569,6 +572,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     H->dev = dev;
     H->fp32 = o.precision == MG_PREC_FP32_REFINE;
     H->nsm = prop.multiProcessorCount;
+    if (o.tile_w > 0 || o.tile_h > 0) H->band_min = 0;  // explicit tiling: use the one-launch step everywhere
     const double km = o.k_variant == 0 ? 1.0 : 0.0;
     {
         cudaError_t e = H->fp32 ? band_prepare<float>() : band_prepare<double>();

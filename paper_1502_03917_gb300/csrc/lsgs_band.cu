@@ -13,12 +13,18 @@
 // step touch a common unknown or residual entry, so a step needs one barrier.
 // Within a colour the updates commute exactly (each residual entry receives one
 // update per phase), so the result equals the sequential multicolour sweep.
+// Each column meets exactly one y phase and one lambda phase per step.
 //
 // Halos.  The final iterate at node (i,j) depends only on the initial data in
 // columns i-28..i+15 and rows j-28..j+15, so a block computes columns
 // [i0-28, i0+W+15) and rows [j0-28, j1+15) and keeps columns [i0, i0+W) and
 // rows [j0, j1); everything outside is recomputed by the neighbouring blocks.
 // The step is out of place (x_in -> x_out) because halos overlap.
+//
+// Storage.  The two fields of a node sit side by side (float2 / double2) in
+// power-of-two row rings, so one shared-memory access moves both fields and a
+// ring slot is a mask.  Nodes whose whole neighbourhood is interior to the grid
+// and to the window take a branch-free path with the constant interior stencil.
 #include <cuda_runtime.h>
 
 #include "band.h"
@@ -28,20 +34,28 @@ namespace aaomg {
 
 namespace {
 
-constexpr int kRing = 40;   // rows of x kept: 32 in use + prefetch distance
-constexpr int kRRing = 32;  // rows of rh in use: tau-31 .. tau-2
-constexpr int kFRing = 16;  // rows of f: prefetched at tau-kPre, used at tau+2
+constexpr int kRing = 64;   // rows of x: tau-31 .. tau+kPre in use
+constexpr int kRRing = 32;  // rows of rh: tau-31 .. tau-2 in use
+constexpr int kFRing = 16;  // rows of f: prefetched at rho-kPre, used at rho+2
 constexpr int kPre = 8;     // prefetch distance in rows
 constexpr int kLag = 31;    // output row = tau - kLag
 
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+    using type = float2;
+};
+template <>
+struct V2<double> {
+    using type = double2;
+};
+
 template <typename T, int WT>
 struct BandSmem {
-    T xy[kRing][WT];
-    T xl[kRing][WT];
-    T ry[kRRing][WT];
-    T rl[kRRing][WT];
-    T fy[kFRing][WT];
-    T fl[kFRing][WT];
+    typename V2<T>::type X[kRing][WT];
+    typename V2<T>::type R[kRRing][WT];
+    typename V2<T>::type F[kFRing][WT];
 };
 
 template <typename T>
@@ -58,7 +72,7 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// shared-memory window of the band: columns [c0, c0+WT), rows [jl, jh]
+// ------------------------------------------------ general (boundary) path --
 template <typename T, int WT>
 struct View {
     BandSmem<T, WT>* S;
@@ -67,25 +81,21 @@ struct View {
         unsigned t = (unsigned)(c - c0);
         return t < (unsigned)WT && j >= jl && j <= jh && c >= 0 && c <= n;
     }
-    __device__ __forceinline__ T& x(int field, int c, int j) const {
-        return field ? S->xl[j % kRing][c - c0] : S->xy[j % kRing][c - c0];
-    }
-    __device__ __forceinline__ T& r(int field, int c, int j) const {
-        return field ? S->rl[j % kRRing][c - c0] : S->ry[j % kRRing][c - c0];
-    }
+    __device__ __forceinline__ typename V2<T>::type& x(int c, int j) const { return S->X[j & (kRing - 1)][c - c0]; }
+    __device__ __forceinline__ typename V2<T>::type& r(int c, int j) const { return S->R[j & (kRRing - 1)][c - c0]; }
 };
 
-// rh = L^{-1}(f - A x) at node (i,j), from the window
 template <typename T, int WT>
-__device__ __forceinline__ void band_resid(const LevelP<T>& P, const View<T, WT>& V, int i, int j) {
+__device__ void band_resid_general(const LevelP<T>& P, const View<T, WT>& V, int i, int j) {
     T m[7], kd[7], y[7], l[7];
     row_coeffs(P, i, j, m, kd);
 #pragma unroll
     for (int o = 0; o < 7; ++o) {
         int ii = i + DI(o), jj = j + DJ(o);
         bool ok = V.has(ii, jj);
-        y[o] = ok ? V.x(0, ii, jj) : T(0);
-        l[o] = ok ? V.x(1, ii, jj) : T(0);
+        typename V2<T>::type v = ok ? V.x(ii, jj) : typename V2<T>::type{T(0), T(0)};
+        y[o] = v.x;
+        l[o] = v.y;
     }
     bool in = node_interior(P, i, j);
     T My, Ky, Ml, Kl, ay, al;
@@ -93,14 +103,12 @@ __device__ __forceinline__ void band_resid(const LevelP<T>& P, const View<T, WT>
     dots(in, m, kd, l, Ml, Kl);
     rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
     T il = inv_ly(P, i, j);
-    T fy = V.S->fy[j % kFRing][i - V.c0], fl = V.S->fl[j % kFRing][i - V.c0];
-    V.r(0, i, j) = (fy - ay) * il;
-    V.r(1, i, j) = (fl - al) * (il * P.invd);
+    typename V2<T>::type fv = V.S->F[j & (kFRing - 1)][i - V.c0];
+    V.r(i, j) = {(fv.x - ay) * il, (fv.y - al) * (il * P.invd)};
 }
 
-// Algorithm 2 update of unknown (field, (i,j)) inside the window
 template <typename T, int WT>
-__device__ __forceinline__ void band_update(const LevelP<T>& P, const View<T, WT>& V, int field, int i, int j) {
+__device__ void band_update_general(const LevelP<T>& P, const View<T, WT>& V, int field, int i, int j) {
     T m[7], kd[7], ry[7], rl[7];
     bool ok[7];
     row_coeffs(P, i, j, m, kd);
@@ -108,8 +116,9 @@ __device__ __forceinline__ void band_update(const LevelP<T>& P, const View<T, WT
     for (int o = 0; o < 7; ++o) {
         int ii = i + DI(o), jj = j + DJ(o);
         ok[o] = V.has(ii, jj);
-        ry[o] = ok[o] ? V.r(0, ii, jj) : T(0);
-        rl[o] = ok[o] ? V.r(1, ii, jj) : T(0);
+        typename V2<T>::type v = ok[o] ? V.r(ii, jj) : typename V2<T>::type{T(0), T(0)};
+        ry[o] = v.x;
+        rl[o] = v.y;
     }
     bool in = node_interior(P, i, j);
     T My, Ky, Ml, Kl, qy, ql;
@@ -117,7 +126,8 @@ __device__ __forceinline__ void band_update(const LevelP<T>& P, const View<T, WT
     dots(in, m, kd, rl, Ml, Kl);
     rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
     T p = (field == 0 ? qy : ql) * inv_n(P, field, i, j);
-    V.x(field, i, j) += p;
+    if (field == 0) V.x(i, j).x += p;
+    else V.x(i, j).y += p;
 #pragma unroll
     for (int o = 0; o < 7; ++o) {
         if (!ok[o]) continue;
@@ -125,14 +135,73 @@ __device__ __forceinline__ void band_update(const LevelP<T>& P, const View<T, WT
         T il = inv_ly(P, ii, jj);
         T mp = m[o] * p;
         T kp = P.c * (kd[o] * p + P.km * mp);
-        if (field == 0) {
-            V.r(0, ii, jj) = ry[o] - mp * il;
-            V.r(1, ii, jj) = rl[o] - kp * (il * P.invd);
-        } else {
-            V.r(0, ii, jj) = ry[o] - kp * il;
-            V.r(1, ii, jj) = rl[o] + mp * il;
-        }
+        if (field == 0) V.r(ii, jj) = {ry[o] - mp * il, rl[o] - kp * (il * P.invd)};
+        else V.r(ii, jj) = {ry[o] - kp * il, rl[o] + mp * il};
     }
+}
+
+// ------------------------------------------------------ interior fast path --
+// constant stencil: m = (mC; mO x6), kd = (4; -1 at E,W,N,S; 0 at NE,SW);
+// in the ring, column offsets are +-1 and row offsets select the slots sm/s/sp
+template <typename T, int WT>
+__device__ __forceinline__ void band_resid_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int t, int sxm, int sx,
+                                                int sxp, int sr, int sf) {
+    auto c0 = S->X[sx][t], e = S->X[sx][t + 1], w = S->X[sx][t - 1];
+    auto nn = S->X[sxp][t], so = S->X[sxm][t], ne = S->X[sxp][t + 1], sw = S->X[sxm][t - 1];
+    T s4y = (e.x + w.x) + (nn.x + so.x), s4l = (e.y + w.y) + (nn.y + so.y);
+    T My = P.mC * c0.x + P.mO * (s4y + (ne.x + sw.x));
+    T Ml = P.mC * c0.y + P.mO * (s4l + (ne.y + sw.y));
+    T Ky = T(4) * c0.x - s4y, Kl = T(4) * c0.y - s4l;
+    T ay, al;
+    rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
+    auto fv = S->F[sf][t];
+    const T il = P.invLy_int;
+    S->R[sr][t] = {(fv.x - ay) * il, (fv.y - al) * (il * P.invd)};
+}
+
+template <typename T, int WT>
+__device__ __forceinline__ void band_update_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int field, int t, int sm,
+                                                 int s, int sp, int sx) {
+    auto r0 = S->R[s][t], e = S->R[s][t + 1], w = S->R[s][t - 1];
+    auto nn = S->R[sp][t], so = S->R[sm][t], ne = S->R[sp][t + 1], sw = S->R[sm][t - 1];
+    T s4y = (e.x + w.x) + (nn.x + so.x), s4l = (e.y + w.y) + (nn.y + so.y);
+    T My = P.mC * r0.x + P.mO * (s4y + (ne.x + sw.x));
+    T Ml = P.mC * r0.y + P.mO * (s4l + (ne.y + sw.y));
+    T Ky = T(4) * r0.x - s4y, Kl = T(4) * r0.y - s4l;
+    T qy, ql;
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    const T il = P.invLy_int, ill = P.invLy_int * P.invd;
+    T p;
+    // per-offset increments of (rh_y, rh_lambda): centre, E/W/N/S, NE/SW
+    T dCy, dCl, dEy, dEl, dDy, dDl;
+    if (field == 0) {
+        p = qy * P.invNy_int;
+        S->X[sx][t].x += p;
+        T mCp = P.mC * p, mOp = P.mO * p;
+        dCy = mCp * il;
+        dEy = mOp * il;
+        dDy = dEy;
+        dCl = P.c * (T(4) * p + P.km * mCp) * ill;
+        dEl = P.c * (-p + P.km * mOp) * ill;
+        dDl = P.c * (P.km * mOp) * ill;
+    } else {
+        p = ql * P.invNl_int;
+        S->X[sx][t].y += p;
+        T mCp = P.mC * p, mOp = P.mO * p;
+        dCy = P.c * (T(4) * p + P.km * mCp) * il;
+        dEy = P.c * (-p + P.km * mOp) * il;
+        dDy = P.c * (P.km * mOp) * il;
+        dCl = -mCp * il;
+        dEl = -mOp * il;
+        dDl = dEl;
+    }
+    S->R[s][t] = {r0.x - dCy, r0.y - dCl};
+    S->R[s][t + 1] = {e.x - dEy, e.y - dEl};
+    S->R[s][t - 1] = {w.x - dEy, w.y - dEl};
+    S->R[sp][t] = {nn.x - dEy, nn.y - dEl};
+    S->R[sm][t] = {so.x - dEy, so.y - dEl};
+    S->R[sp][t + 1] = {ne.x - dDy, ne.y - dDl};
+    S->R[sm][t - 1] = {sw.x - dDy, sw.y - dDl};
 }
 
 template <typename T, int WT>
@@ -146,48 +215,84 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
     const int c0 = i0 - kBandHL;
     const int c = c0 + tid;
     const bool col_in = c >= 0 && c <= P.n;
+    // The outermost window columns only supply data: by the dependency reach
+    // no kept node uses an update or a residual formed on them, so they are
+    // not computed (which keeps every warp on the same path).
+    const bool col_work = col_in && tid >= 1 && tid <= WT - 2;
     const int j0 = blockIdx.y * Hs;
     const int j1 = min(j0 + Hs, P.n + 1);
     const int jl = max(0, j0 - kBandHL);
     const int jh = min(P.n, j1 - 1 + kBandHR);
-    View<T, WT> V{S, c0, jl, jh, P.n};
+    const View<T, WT> V{S, c0, jl, jh, P.n};
+    // this column (and its neighbours) interior to the grid and the window
+    const bool col_fast = c >= 2 && c <= P.n - 2;
+    const int jfl = max(2, jl + 1), jfh = min(P.n - 2, jh - 1);  // rows whose neighbourhood is fast
 
-    for (int r = 0; r < kRing; ++r) S->xy[r][tid] = S->xl[r][tid] = T(0);
-    for (int r = 0; r < kRRing; ++r) S->ry[r][tid] = S->rl[r][tid] = T(0);
-    for (int r = 0; r < kFRing; ++r) S->fy[r][tid] = S->fl[r][tid] = T(0);
+    using V2T = typename V2<T>::type;
+    for (int r = 0; r < kRing; ++r) S->X[r][tid] = V2T{T(0), T(0)};
+    for (int r = 0; r < kRRing; ++r) S->R[r][tid] = V2T{T(0), T(0)};
+    for (int r = 0; r < kFRing; ++r) S->F[r][tid] = V2T{T(0), T(0)};
     __syncthreads();
 
-    // one commit group per row, also when the row is outside the window
+    // one commit group per row, also for rows outside the window
+    const T* xin_c = xin + c;
+    const T* f_c = f + c;
     auto issue = [&](int row) {
         if (col_in && row >= jl && row <= jh) {
-            int64_t g = (int64_t)row * P.ld + c;
-            cp_async(&S->xy[row % kRing][tid], xin + g);
-            cp_async(&S->xl[row % kRing][tid], xin + g + P.fs);
-            cp_async(&S->fy[row % kFRing][tid], f + g);
-            cp_async(&S->fl[row % kFRing][tid], f + g + P.fs);
+            int64_t g = (int64_t)row * P.ld;
+            T* xs = reinterpret_cast<T*>(&S->X[row & (kRing - 1)][tid]);
+            T* fs = reinterpret_cast<T*>(&S->F[row & (kFRing - 1)][tid]);
+            cp_async(xs, xin_c + g);
+            cp_async(xs + 1, xin_c + g + P.fs);
+            cp_async(fs, f_c + g);
+            cp_async(fs + 1, f_c + g + P.fs);
         }
         cp_async_commit();
     };
     for (int row = jl; row < jl + kPre; ++row) issue(row);
-    cp_async_wait<kPre - 1>();  // row jl is in
+    cp_async_wait<kPre - 1>();  // row jl has landed
     __syncthreads();
 
     const int cm7 = ((c % 7) + 7) % 7;
+    int tm7 = jl % 7;
     for (int tau = jl; tau <= j1 - 1 + kLag; ++tau) {
         issue(tau + kPre);
-        const int rho = tau - 2;
-        if (col_in && rho >= jl && rho <= jh) band_resid<T, WT>(P, V, c, rho);
-        // the y phase and the lambda phase that meet this column at this step
-        const int ts = (5 * ((cm7 + 2 * (tau % 7) + 6) % 7)) % 7;
-        const int jy = tau - 4 - 2 * ts, jlam = tau - 18 - 2 * ts;
-        if (col_in && jy >= jl && jy <= jh) band_update<T, WT>(P, V, 0, c, jy);
-        if (col_in && jlam >= jl && jlam <= jh) band_update<T, WT>(P, V, 1, c, jlam);
-        const int ro = tau - kLag;
-        if (ro >= j0 && ro < j1 && c >= i0 && c < i1) {
-            int64_t g = (int64_t)ro * P.ld + c;
-            xout[g] = S->xy[ro % kRing][tid];
-            xout[g + P.fs] = S->xl[ro % kRing][tid];
+        if (col_work) {
+            // rh of row rho = tau - 2 from the original iterate
+            const int rho = tau - 2;
+            if (rho >= jl && rho <= jh) {
+                if (col_fast && rho >= jfl && rho <= jfh)
+                    band_resid_fast<T, WT>(P, S, tid, (rho - 1) & (kRing - 1), rho & (kRing - 1),
+                                           (rho + 1) & (kRing - 1), rho & (kRRing - 1), rho & (kFRing - 1));
+                else
+                    band_resid_general<T, WT>(P, V, c, rho);
+            }
+            // the y phase and the lambda phase that meet this column at this step
+            const int ts = (5 * ((cm7 + 2 * tm7 + 6) % 7)) % 7;
+            const int jy = tau - 4 - 2 * ts, jlam = jy - 14;
+            if (jy >= jl && jy <= jh) {
+                if (col_fast && jy >= jfl && jy <= jfh)
+                    band_update_fast<T, WT>(P, S, 0, tid, (jy - 1) & (kRRing - 1), jy & (kRRing - 1),
+                                            (jy + 1) & (kRRing - 1), jy & (kRing - 1));
+                else
+                    band_update_general<T, WT>(P, V, 0, c, jy);
+            }
+            if (jlam >= jl && jlam <= jh) {
+                if (col_fast && jlam >= jfl && jlam <= jfh)
+                    band_update_fast<T, WT>(P, S, 1, tid, (jlam - 1) & (kRRing - 1), jlam & (kRRing - 1),
+                                            (jlam + 1) & (kRRing - 1), jlam & (kRing - 1));
+                else
+                    band_update_general<T, WT>(P, V, 1, c, jlam);
+            }
+            const int ro = tau - kLag;
+            if (ro >= j0 && ro < j1 && c >= i0 && c < i1) {
+                int64_t g = (int64_t)ro * P.ld + c;
+                V2T v = S->X[ro & (kRing - 1)][tid];
+                xout[g] = v.x;
+                xout[g + P.fs] = v.y;
+            }
         }
+        tm7 = tm7 == 6 ? 0 : tm7 + 1;
         cp_async_wait<kPre - 1>();  // row tau + 1 has landed
         __syncthreads();
     }
