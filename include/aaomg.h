@@ -90,6 +90,8 @@ typedef struct mg_options {
     int profile;      /* 1: time the finest-level smoothing inside every iteration (CUDA events) */
     int tile_w;       /* LSGS step kernel: owned columns per block; <= 0: widest the block allows */
     int tile_h;       /* LSGS step kernel: owned rows per block; <= 0: chosen to fill the GPU */
+    int small_max;    /* levels with at most this many nodes per side smooth in one launch per
+                         smoothing call (one block or one cluster); 0: 1025; < 0: never */
 } mg_options;
 
 /* Build the hierarchy for h = 2^-levels (1 <= levels <= 13; level 1 is the

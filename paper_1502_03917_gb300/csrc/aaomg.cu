@@ -16,6 +16,7 @@
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
+#include "small.h"
 
 using namespace aaomg;
 
@@ -174,6 +175,8 @@ struct mg_ctx {
     int dev = 0;
     int nsm = 152;
     int band_min = 257;       // levels with at least this many nodes per side use the one-launch LSGS step
+    int small_max = 1025;     // levels up to this many nodes per side: one launch per smoothing call
+    int csize = 1;            // cluster size of the one-launch smoothing kernel
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -255,6 +258,20 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* x = (T*)v.x;
     T* f = (T*)v.f;
     T* rh = (T*)v.rh;
+    if (v.n + 1 <= H->small_max) {
+        // the whole smoothing call in one launch: one block when rh fits in
+        // shared memory, else one cluster over L2-resident data
+        if (block_smooth_smem<T>(v.n) <= (size_t)kBlockSmemMax) {
+            launch_smooth_block<T>(P, H->o.smoother, steps, x, f, s);
+            H->rec_kernels += 1;
+            return;
+        }
+        if (H->csize >= 2) {
+            launch_smooth_cluster<T>(P, H->o.smoother, steps, x, f, rh, H->csize, s);
+            H->rec_kernels += 1;
+            return;
+        }
+    }
     switch (H->o.smoother) {
     case MG_SMOOTHER_NE:
         for (int m = 0; m < steps; ++m) {
@@ -572,7 +589,21 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     H->dev = dev;
     H->fp32 = o.precision == MG_PREC_FP32_REFINE;
     H->nsm = prop.multiProcessorCount;
-    if (o.tile_w > 0 || o.tile_h > 0) H->band_min = 0;  // explicit tiling: use the one-launch step everywhere
+    if (o.small_max != 0) H->small_max = o.small_max;
+    if (o.tile_w > 0 || o.tile_h > 0) {  // explicit tiling: the one-launch LSGS step on every level
+        H->band_min = 0;
+        H->small_max = -1;
+    } else {
+        H->band_min = H->small_max + 1 > 257 ? H->small_max + 1 : 257;
+    }
+    {
+        cudaError_t e = H->fp32 ? small_prepare<float>() : small_prepare<double>();
+        if (e != cudaSuccess) {
+            delete H;
+            return fail(AAOMG_ERR_CUDA, std::string("smoothing kernel attributes: ") + cudaGetErrorString(e));
+        }
+        H->csize = H->fp32 ? max_cluster_size<float>() : max_cluster_size<double>();
+    }
     const double km = o.k_variant == 0 ? 1.0 : 0.0;
     {
         cudaError_t e = H->fp32 ? band_prepare<float>() : band_prepare<double>();

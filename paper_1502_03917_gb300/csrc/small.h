@@ -1,0 +1,34 @@
+// small.h -- one-launch smoothing calls for small and middle levels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace aaomg {
+
+// threads per block of the one-launch smoothing kernels (FP64 needs more
+// registers per thread)
+template <typename T>
+constexpr int small_threads() {
+    return sizeof(T) == 4 ? 1024 : 512;
+}
+constexpr int kBlockSmemMax = 227 * 1024;
+
+// shared memory of the single-block kernel for a level with n cells
+template <typename T>
+size_t block_smooth_smem(int n);
+template <typename T>
+cudaError_t small_prepare();
+// `steps` smoothing steps (smoother 0 NE, 1 LSGS, 2 sLSGS) on one level in one
+// launch: one thread block (rh in shared memory) ...
+template <typename T>
+void launch_smooth_block(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, cudaStream_t s);
+// ... or one cluster of `csize` blocks (x, f, rh in global memory / L2)
+template <typename T>
+cudaError_t launch_smooth_cluster(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, T* rh, int csize,
+                                  cudaStream_t s);
+// largest cluster size (16, 8, ...) the device can schedule for that kernel
+template <typename T>
+int max_cluster_size();
+
+}  // namespace aaomg

@@ -63,6 +63,25 @@ def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("L,small_max", [(6, 0), (8, 0), (10, 0), (6, -1), (8, -1), (9, 300)])
+def test_smoothing_call_kernels(mg, oracle_mod, L, small_max, smoother, precision):
+    """The one-launch smoothing call (one block with the residual in shared
+    memory, or one cluster over L2-resident data) and the per-phase launches
+    (small_max = -1) give the oracle's steps."""
+    alpha = 1e-2
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 500 + L))
+    f = inputs.f32_exact(inputs.x_uniform(L, 600 + L))
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother)
+    with mg.Solver(L, alpha, smoother=smoother, precision=precision, small_max=small_max) as s:
+        for steps in (1, 2):
+            x = dev(x0)
+            s.smooth(dev(f), x, steps)
+            d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
+            assert d <= TOL[precision], (steps, d)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("tile", [(0, 0), (20, 9), (1, 1), (57, 130), (3, 40)])
 @pytest.mark.parametrize("L", [2, 4, 8])
 def test_lsgs_step_kernel_tiling(mg, oracle_mod, L, tile, precision):
