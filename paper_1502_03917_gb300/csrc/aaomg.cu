@@ -43,12 +43,24 @@ struct Lev {
     void* f = nullptr;
     void* rh = nullptr;
     BandGrid bg{};
+    EdgeTable<float> ef{};   // tabulated edge nodes for the single-block smoothing kernel
+    EdgeTable<double> ed{};
     LevelP<float> pf{};
     LevelP<double> pd{};
 };
 
 template <typename T>
 const LevelP<T>& lp(const Lev& v);
+template <typename T>
+const EdgeTable<T>& etab(const Lev& v);
+template <>
+const EdgeTable<float>& etab<float>(const Lev& v) {
+    return v.ef;
+}
+template <>
+const EdgeTable<double>& etab<double>(const Lev& v) {
+    return v.ed;
+}
 template <typename T>
 const CtaParams<T>& ctap(const mg_ctx* H);
 template <>
@@ -58,6 +70,37 @@ const LevelP<float>& lp<float>(const Lev& v) {
 template <>
 const LevelP<double>& lp<double>(const Lev& v) {
     return v.pd;
+}
+
+// Scalar coefficients of a level: L_y and N_ii of node (i,j) (FP64).
+struct Coef {
+    int n;
+    double h2, beta, c, d, km;
+};
+Coef make_coef(int n, double alpha, bool scaled, double km) {
+    double h = 1.0 / n, beta = std::sqrt(alpha);
+    return Coef{n, h * h, beta, scaled ? beta : 1.0, scaled ? 1.0 : 1.0 / alpha, km};
+}
+void coef_row(const Coef& K, int i, int j, double m[7], double k[7]) {
+    double kd[7];
+    row_coeffs_general<double>(i, j, K.n, K.h2, m, kd);
+    for (int o = 0; o < 7; ++o) k[o] = kd[o] + K.km * m[o];
+}
+double coef_ly(const Coef& K, int i, int j) {
+    double m[7], k[7];
+    coef_row(K, i, j, m, k);
+    return m[0] + K.beta * k[0];
+}
+double coef_nd(const Coef& K, int i, int j, int field) {
+    double m[7], k[7], s = 0.0;
+    coef_row(K, i, j, m, k);
+    for (int o = 0; o < 7; ++o) {
+        int ii = i + DI(o), jj = j + DJ(o);
+        if (!in_grid(ii, jj, K.n)) continue;
+        double num = field == 0 ? m[o] * m[o] + K.c * K.c * k[o] * k[o] / K.d : K.c * K.c * k[o] * k[o] + K.d * m[o] * m[o];
+        s += num / coef_ly(K, ii, jj);
+    }
+    return s;
 }
 
 // Coefficients of one level in the parametrised form A = [[M, cK], [cK, -dM]],
@@ -77,27 +120,9 @@ LevelP<T> make_params(int n, int ld, int64_t fs, double alpha, bool scaled, doub
     P.beta = (T)beta;
     P.km = (T)km;
     P.tau = (T)tau;
-    auto coeffs = [&](int i, int j, double m[7], double k[7]) {
-        double kd[7];
-        row_coeffs_general<double>(i, j, n, h2, m, kd);
-        for (int o = 0; o < 7; ++o) k[o] = kd[o] + km * m[o];
-    };
-    auto Ly = [&](int i, int j) {
-        double m[7], k[7];
-        coeffs(i, j, m, k);
-        return m[0] + beta * k[0];
-    };
-    auto Nd = [&](int i, int j, int field) {
-        double m[7], k[7], s = 0.0;
-        coeffs(i, j, m, k);
-        for (int o = 0; o < 7; ++o) {
-            int ii = i + DI(o), jj = j + DJ(o);
-            if (!in_grid(ii, jj, n)) continue;
-            double num = field == 0 ? m[o] * m[o] + c * c * k[o] * k[o] / d : c * c * k[o] * k[o] + d * m[o] * m[o];
-            s += num / Ly(ii, jj);
-        }
-        return s;
-    };
+    const Coef K = make_coef(n, alpha, scaled, km);
+    auto Ly = [&](int i, int j) { return coef_ly(K, i, j); };
+    auto Nd = [&](int i, int j, int field) { return coef_nd(K, i, j, field); };
     {
         double m[7], kd[7];
         row_coeffs_general<double>(1, 1, n, h2, m, kd);
@@ -174,9 +199,10 @@ struct mg_ctx {
     mg_options o{};
     int dev = 0;
     int nsm = 152;
-    int band_min = 257;       // levels with at least this many nodes per side use the one-launch LSGS step
-    int small_max = 1025;     // levels up to this many nodes per side: one launch per smoothing call
+    int band_min = 2049;      // levels with at least this many nodes per side use the one-launch LSGS step
+    int small_max = 129;      // levels up to this many nodes per side: one launch per smoothing call
     int csize = 1;            // cluster size of the one-launch smoothing kernel
+    bool use_cluster = false; // middle levels: one cluster launch instead of per-phase launches
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -262,11 +288,11 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
         // the whole smoothing call in one launch: one block when rh fits in
         // shared memory, else one cluster over L2-resident data
         if (block_smooth_smem<T>(v.n) <= (size_t)kBlockSmemMax) {
-            launch_smooth_block<T>(P, H->o.smoother, steps, x, f, s);
+            launch_smooth_block<T>(P, etab<T>(v), H->o.smoother, steps, x, f, s);
             H->rec_kernels += 1;
             return;
         }
-        if (H->csize >= 2) {
+        if (H->csize >= 2 && H->use_cluster) {
             launch_smooth_cluster<T>(P, H->o.smoother, steps, x, f, rh, H->csize, s);
             H->rec_kernels += 1;
             return;
@@ -377,6 +403,67 @@ int record_iteration(mg_ctx* H, cudaStream_t s) {
         launch_refine_update(H->fine64, H->x64, (const float*)v.x, v.ld, v.fs, s);
         H->rec_kernels += 1;
     }
+    return AAOMG_OK;
+}
+
+// Tabulated edge nodes of level v (see edge.h), in the cycle's precision.
+template <typename T>
+int build_edge_table(mg_ctx* H, Lev& v, double km, EdgeTable<T>& E) {
+    const int n = v.n;
+    const Coef K = make_coef(n, H->alpha, H->fp32, km);
+    std::vector<int> nodes[7];
+    for (int j = 0; j <= n; ++j)
+        for (int i = 0; i <= n; ++i)
+            if (i < 2 || i > n - 2 || j < 2 || j > n - 2) nodes[(i + 2 * j) % 7].push_back(j * (n + 1) + i);
+    int total = 0;
+    for (int c = 0; c < 7; ++c) {
+        E.start[c] = total;
+        E.count[c] = (int)nodes[c].size();
+        total += E.count[c];
+    }
+    E.total = total;
+    std::vector<T> m(7 * (size_t)total), kd(7 * (size_t)total), il(7 * (size_t)total), iny(total), inl(total);
+    std::vector<int> node(total), mask(total);
+    int e = 0;
+    for (int c = 0; c < 7; ++c)
+        for (int p : nodes[c]) {
+            int i = p % (n + 1), j = p / (n + 1);
+            double mm[7], kk[7];
+            row_coeffs_general<double>(i, j, n, K.h2, mm, kk);
+            int mk = 0;
+            for (int o = 0; o < 7; ++o) {
+                int ii = i + DI(o), jj = j + DJ(o);
+                bool in = in_grid(ii, jj, n);
+                if (in) mk |= 1 << o;
+                m[(size_t)o * total + e] = (T)mm[o];
+                kd[(size_t)o * total + e] = (T)kk[o];
+                il[(size_t)o * total + e] = in ? (T)(1.0 / coef_ly(K, ii, jj)) : T(0);
+            }
+            node[e] = p;
+            mask[e] = mk;
+            iny[e] = (T)(1.0 / coef_nd(K, i, j, 0));
+            inl[e] = (T)(1.0 / coef_nd(K, i, j, 1));
+            ++e;
+        }
+    size_t tb = sizeof(T) * (size_t)total, ib = sizeof(int) * (size_t)total;
+    void* buf = nullptr;
+    int rc = dalloc(H, &buf, 23 * tb + 2 * ib);
+    if (rc) return rc;
+    char* b = (char*)buf;
+    E.m = (T*)b;
+    E.kd = (T*)(b + 7 * tb);
+    E.il = (T*)(b + 14 * tb);
+    E.inv_ny = (T*)(b + 21 * tb);
+    E.inv_nl = (T*)(b + 22 * tb);
+    E.node = (int*)(b + 23 * tb);
+    E.mask = (int*)(b + 23 * tb + ib);
+    CK(cudaMemcpy(E.m, m.data(), 7 * tb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.kd, kd.data(), 7 * tb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.il, il.data(), 7 * tb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.inv_ny, iny.data(), tb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.inv_nl, inl.data(), tb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.node, node.data(), ib, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.mask, mask.data(), ib, cudaMemcpyHostToDevice));
     return AAOMG_OK;
 }
 
@@ -594,7 +681,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         H->band_min = 0;
         H->small_max = -1;
     } else {
-        H->band_min = H->small_max + 1 > 257 ? H->small_max + 1 : 257;
+        H->band_min = H->small_max + 1 > 2049 ? H->small_max + 1 : 2049;
     }
     {
         cudaError_t e = H->fp32 ? small_prepare<float>() : small_prepare<double>();

@@ -7,6 +7,7 @@
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
+#include "lean.cuh"
 #include "stencil.cuh"
 
 namespace aaomg {
@@ -15,22 +16,42 @@ namespace {
 
 // ---------------------------------------------------------------- kernels --
 
-// rh = L^{-1} (f - A x)
+// Thread t of the launch -> node: the deep-interior nodes first (their count
+// rounded up to a warp), then the edge nodes, so that no warp mixes the
+// constant-stencil path with the general one.
+
+// rh = L^{-1} (f - A x) on every node
 template <typename T>
 __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ rh) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > P.n || j > P.n) return;
-    resid_hat_at(P, f, x, rh, i, j);
+    InteriorAll ia(P.n);
+    EdgeNodes ed(P.n, -1);
+    const int ni = ia.count(), nip = (ni + 31) & ~31;
+    int t = blockIdx.x * blockDim.x + threadIdx.x, i, j;
+    if (t < nip) {
+        if (t < ni) {
+            ia.node(t, i, j);
+            resid_fast(P, f, x, rh, i, j);
+        }
+    } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
+        resid_hat_at(P, f, x, rh, i, j);
+    }
 }
 
 // Algorithm 1 update: x += tau L^{-1} A rh (A symmetric), with rh = L^{-1} r
 template <typename T>
 __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict__ rh) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i > P.n || j > P.n) return;
-    ne_update_at(P, x, rh, i, j);
+    InteriorAll ia(P.n);
+    EdgeNodes ed(P.n, -1);
+    const int ni = ia.count(), nip = (ni + 31) & ~31;
+    int t = blockIdx.x * blockDim.x + threadIdx.x, i, j;
+    if (t < nip) {
+        if (t < ni) {
+            ia.node(t, i, j);
+            ne_fast(P, x, rh, i, j);
+        }
+    } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
+        ne_update_at(P, x, rh, i, j);
+    }
 }
 
 // One colour phase of Algorithm 2: every unknown of field `field` on a node of
@@ -39,11 +60,15 @@ __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict_
 // neighbour, so the updates of a phase are independent and race-free.
 template <typename T>
 __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__ x, T* __restrict__ rh) {
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (j > P.n) return;
-    int i = ((colour - 2 * j) % 7 + 7) % 7 + 7 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (i > P.n) return;
-    lsgs_update_at(P, field, x, rh, i, j);
+    InteriorColour ic(P.n, colour);
+    EdgeNodes ed(P.n, colour);
+    const int ni = ic.count(), nip = (ni + 31) & ~31;
+    int t = blockIdx.x * blockDim.x + threadIdx.x, i, j;
+    if (t < nip) {
+        if (t < ni && ic.node(t, i, j)) lsgs_fast(P, field, x, rh, i, j);
+    } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
+        lsgs_update_at(P, field, x, rh, i, j);
+    }
 }
 
 // Defect restriction: fc = P^T (f - A x) on a coarse node (I,J) -- weight 1 at
@@ -226,17 +251,28 @@ inline dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (n
 // ------------------------------------------------------------- launchers --
 const dim3 kBlk2(32, 8);
 
+// threads for the interior/edge split: interior slots rounded to a warp + edge slots
+inline int split_threads(int n, bool colour) {
+    int ni = n >= 4 ? (n - 3) * (colour ? (n - 3 + 6) / 7 : (n - 3)) : 0;
+    int rows = n >= 4 ? 4 : n + 1;
+    int full = colour ? (n + 7) / 7 : n + 1;
+    int ne = rows * full + (n >= 4 ? 4 * (n - 3) : 0);
+    return ((ni + 31) & ~31) + ne;
+}
 template <typename T>
 void launch_resid_hat(const LevelP<T>& P, const T* f, const T* x, T* rh, cudaStream_t s) {
-    k_resid_hat<T><<<grid2(P.n + 1, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, f, x, rh);
+    int nt = split_threads(P.n, false);
+    k_resid_hat<T><<<(nt + 255) / 256, 256, 0, s>>>(P, f, x, rh);
 }
 template <typename T>
 void launch_ne_update(const LevelP<T>& P, T* x, const T* rh, cudaStream_t s) {
-    k_ne_update<T><<<grid2(P.n + 1, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, x, rh);
+    int nt = split_threads(P.n, false);
+    k_ne_update<T><<<(nt + 255) / 256, 256, 0, s>>>(P, x, rh);
 }
 template <typename T>
 void launch_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, T* rh, cudaStream_t s) {
-    k_lsgs_phase<T><<<grid2((P.n + 7) / 7, P.n + 1, kBlk2), kBlk2, 0, s>>>(P, field, colour, x, rh);
+    int nt = split_threads(P.n, true);
+    k_lsgs_phase<T><<<(nt + 255) / 256, 256, 0, s>>>(P, field, colour, x, rh);
 }
 template <typename T>
 void launch_restrict(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* f, const T* x, T* fc, T* xc, cudaStream_t s) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "edge.h"
 
 namespace aaomg {
 
@@ -22,7 +23,8 @@ cudaError_t small_prepare();
 // `steps` smoothing steps (smoother 0 NE, 1 LSGS, 2 sLSGS) on one level in one
 // launch: one thread block (rh in shared memory) ...
 template <typename T>
-void launch_smooth_block(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, cudaStream_t s);
+void launch_smooth_block(const LevelP<T>& P, const EdgeTable<T>& E, int smoother, int steps, T* x, const T* f,
+                         cudaStream_t s);
 // ... or one cluster of `csize` blocks (x, f, rh in global memory / L2)
 template <typename T>
 cudaError_t launch_smooth_cluster(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, T* rh, int csize,

@@ -17,6 +17,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "edge.h"
+#include "lean.cuh"
 #include "small.h"
 #include "stencil.cuh"
 
@@ -32,6 +34,108 @@ struct BlockSync {
 struct ClusterSync {
     __device__ __forceinline__ void operator()() const { cg::this_cluster().sync(); }
 };
+
+// ----------------------------------------------- tabulated edge updates --
+template <typename T>
+struct EdgeRow {
+    int p, mask;
+    T m[7], kd[7];
+};
+
+template <typename T>
+__device__ __forceinline__ void edge_load(const EdgeTable<T>& E, int e, EdgeRow<T>& r) {
+    r.p = E.node[e];
+    r.mask = E.mask[e];
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        r.m[o] = E.m[o * E.total + e];
+        r.kd[o] = E.kd[o * E.total + e];
+    }
+}
+
+__device__ __forceinline__ int edge_off(int o, int ld) {
+    return DI(o) + DJ(o) * ld;
+}
+
+template <typename T>
+__device__ __forceinline__ void edge_gather(const EdgeRow<T>& r, const T* v, int ld, T& Mv, T& Kv) {
+    Mv = T(0);
+    Kv = T(0);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        T a = ((r.mask >> o) & 1) ? v[r.p + edge_off(o, ld)] : T(0);
+        Mv += r.m[o] * a;
+        Kv += r.kd[o] * a;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void resid_edge(const LevelP<T>& P, const EdgeTable<T>& E, int e, const T* f, const T* x,
+                                           T* rh) {
+    EdgeRow<T> r;
+    edge_load(E, e, r);
+    T My, Ky, Ml, Kl, ay, al;
+    edge_gather(r, x, P.ld, My, Ky);
+    edge_gather(r, x + P.fs, P.ld, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
+    const T il = E.il[e];  // offset 0 is the node itself
+    rh[r.p] = (f[r.p] - ay) * il;
+    rh[r.p + P.fs] = (f[r.p + P.fs] - al) * (il * P.invd);
+}
+
+template <typename T>
+__device__ __forceinline__ void ne_edge(const LevelP<T>& P, const EdgeTable<T>& E, int e, T* x, const T* rh) {
+    EdgeRow<T> r;
+    edge_load(E, e, r);
+    T My, Ky, Ml, Kl, qy, ql;
+    edge_gather(r, rh, P.ld, My, Ky);
+    edge_gather(r, rh + P.fs, P.ld, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    const T il = E.il[e];
+    x[r.p] += P.tau * il * qy;
+    x[r.p + P.fs] += P.tau * (il * P.invd) * ql;
+}
+
+template <typename T>
+__device__ __forceinline__ void lsgs_edge(const LevelP<T>& P, const EdgeTable<T>& E, int e, int field, T* x,
+                                          T* rh) {
+    EdgeRow<T> r;
+    edge_load(E, e, r);
+    T ry[7], rl[7];
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        bool v = (r.mask >> o) & 1;
+        ry[o] = v ? rh[r.p + edge_off(o, P.ld)] : T(0);
+        rl[o] = v ? rh[r.p + edge_off(o, P.ld) + P.fs] : T(0);
+    }
+    T My = T(0), Ky = T(0), Ml = T(0), Kl = T(0);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        My += r.m[o] * ry[o];
+        Ky += r.kd[o] * ry[o];
+        Ml += r.m[o] * rl[o];
+        Kl += r.kd[o] * rl[o];
+    }
+    T qy, ql;
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    T p = field == 0 ? qy * E.inv_ny[e] : ql * E.inv_nl[e];
+    x[r.p + (field ? P.fs : 0)] += p;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        if (!((r.mask >> o) & 1)) continue;
+        const int q = r.p + edge_off(o, P.ld);
+        const T il = E.il[o * E.total + e];
+        T mp = r.m[o] * p;
+        T kp = P.c * (r.kd[o] * p + P.km * mp);
+        if (field == 0) {
+            rh[q] = ry[o] - mp * il;
+            rh[q + P.fs] = rl[o] - kp * (il * P.invd);
+        } else {
+            rh[q] = ry[o] - kp * il;
+            rh[q + P.fs] = rl[o] + mp * il;
+        }
+    }
+}
 
 // Gather of v at the 7 offsets through an L2 load (cluster variant).
 template <typename T>
@@ -113,24 +217,49 @@ __device__ __forceinline__ void lsgs_update_l2(const LevelP<T>& P, int field, T*
 // phase loops shared by both kernels; `sync` separates dependent phases,
 // `g`/`G` are the thread's rank and the thread count of the group
 template <typename T, bool L2, typename Sync>
-__device__ void smooth_loop(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, T* rh, int g, int G,
-                            Sync sync) {
+__device__ void smooth_loop(const LevelP<T>& P, const EdgeTable<T>& E, int smoother, int steps, T* x, const T* f,
+                            T* rh, int g, int G, Sync sync) {
     const int n1 = P.n + 1, nn = n1 * n1;
+    // the deep-interior nodes (warp-rounded) first, then the edge nodes: a warp
+    // never mixes the constant-stencil path with the general one (L1 variant)
+    const InteriorAll ia(P.n);
+    const int nia = ia.count(), niap = (nia + 31) & ~31, nea = E.total;
     auto resid_all = [&]() {
-        for (int t = g; t < nn; t += G) {
-            if (L2) resid_hat_l2(P, f, x, rh, t % n1, t / n1);
-            else resid_hat_at(P, f, x, rh, t % n1, t / n1);
+        if (L2) {
+            for (int t = g; t < nn; t += G) resid_hat_l2(P, f, x, rh, t % n1, t / n1);
+        } else {
+            for (int t = g; t < niap + nea; t += G) {
+                int i, j;
+                if (t < niap) {
+                    if (t < nia) {
+                        ia.node(t, i, j);
+                        resid_fast(P, f, x, rh, i, j);
+                    }
+                } else {
+                    resid_edge(P, E, t - niap, f, x, rh);
+                }
+            }
         }
         sync();
     };
     auto phase = [&](int field, int colour) {
-        const int cpr = (n1 + 6) / 7;
-        for (int t = g; t < n1 * cpr; t += G) {
-            int j = t / cpr, k = t - j * cpr;
-            int i = ((colour - 2 * j) % 7 + 7) % 7 + 7 * k;
-            if (i <= P.n) {
-                if (L2) lsgs_update_l2(P, field, x, rh, i, j);
-                else lsgs_update_at(P, field, x, rh, i, j);
+        if (L2) {
+            const int cpr = (n1 + 6) / 7;
+            for (int t = g; t < n1 * cpr; t += G) {
+                int j = t / cpr, k = t - j * cpr;
+                int i = ((colour - 2 * j) % 7 + 7) % 7 + 7 * k;
+                if (i <= P.n) lsgs_update_l2(P, field, x, rh, i, j);
+            }
+        } else {
+            const InteriorColour ic(P.n, colour);
+            const int ni = ic.count(), nip = (ni + 31) & ~31, ne = E.count[colour], e0 = E.start[colour];
+            for (int t = g; t < nip + ne; t += G) {
+                int i, j;
+                if (t < nip) {
+                    if (t < ni && ic.node(t, i, j)) lsgs_fast(P, field, x, rh, i, j);
+                } else {
+                    lsgs_edge(P, E, e0 + t - nip, field, x, rh);
+                }
             }
         }
         sync();
@@ -138,9 +267,20 @@ __device__ void smooth_loop(const LevelP<T>& P, int smoother, int steps, T* x, c
     if (smoother == 0) {
         for (int m = 0; m < steps; ++m) {
             resid_all();
-            for (int t = g; t < nn; t += G) {
-                if (L2) ne_update_l2(P, x, rh, t % n1, t / n1);
-                else ne_update_at(P, x, rh, t % n1, t / n1);
+            if (L2) {
+                for (int t = g; t < nn; t += G) ne_update_l2(P, x, rh, t % n1, t / n1);
+            } else {
+                for (int t = g; t < niap + nea; t += G) {
+                    int i, j;
+                    if (t < niap) {
+                        if (t < nia) {
+                            ia.node(t, i, j);
+                            ne_fast(P, x, rh, i, j);
+                        }
+                    } else {
+                        ne_edge(P, E, t - niap, x, rh);
+                    }
+                }
             }
             sync();
         }
@@ -157,11 +297,11 @@ __device__ void smooth_loop(const LevelP<T>& P, int smoother, int steps, T* x, c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(small_threads<T>()) k_smooth_block(LevelP<T> P, int smoother, int steps, T* x,
-                                                                     const T* __restrict__ f) {
+__global__ void __launch_bounds__(small_threads<T>()) k_smooth_block(LevelP<T> P, EdgeTable<T> E, int smoother,
+                                                                     int steps, T* x, const T* __restrict__ f) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* rh = reinterpret_cast<T*>(smem_raw);  // layout of P (ld = n+1, fs = (n+1)^2)
-    smooth_loop<T, false>(P, smoother, steps, x, f, rh, threadIdx.x, blockDim.x, BlockSync{});
+    smooth_loop<T, false>(P, E, smoother, steps, x, f, rh, threadIdx.x, blockDim.x, BlockSync{});
 }
 
 template <typename T>
@@ -170,7 +310,7 @@ __global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T>
     cg::cluster_group cl = cg::this_cluster();
     int g = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
     int G = (int)(cl.num_blocks() * blockDim.x);
-    smooth_loop<T, true>(P, smoother, steps, x, f, rh, g, G, ClusterSync{});
+    smooth_loop<T, true>(P, EdgeTable<T>{}, smoother, steps, x, f, rh, g, G, ClusterSync{});
 }
 
 }  // namespace
@@ -188,8 +328,9 @@ cudaError_t small_prepare() {
 }
 
 template <typename T>
-void launch_smooth_block(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, cudaStream_t s) {
-    k_smooth_block<T><<<1, small_threads<T>(), block_smooth_smem<T>(P.n), s>>>(P, smoother, steps, x, f);
+void launch_smooth_block(const LevelP<T>& P, const EdgeTable<T>& E, int smoother, int steps, T* x, const T* f,
+                         cudaStream_t s) {
+    k_smooth_block<T><<<1, small_threads<T>(), block_smooth_smem<T>(P.n), s>>>(P, E, smoother, steps, x, f);
 }
 
 template <typename T>
@@ -235,7 +376,8 @@ int max_cluster_size() {
 #define AAOMG_SMALL_INST(T)                                                                                       \
     template size_t block_smooth_smem<T>(int);                                                                    \
     template cudaError_t small_prepare<T>();                                                                      \
-    template void launch_smooth_block<T>(const LevelP<T>&, int, int, T*, const T*, cudaStream_t);                 \
+    template void launch_smooth_block<T>(const LevelP<T>&, const EdgeTable<T>&, int, int, T*, const T*,           \
+                                         cudaStream_t);                                                           \
     template cudaError_t launch_smooth_cluster<T>(const LevelP<T>&, int, int, T*, const T*, T*, int, cudaStream_t); \
     template int max_cluster_size<T>();
 AAOMG_SMALL_INST(float)
