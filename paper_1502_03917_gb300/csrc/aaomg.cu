@@ -726,6 +726,17 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         mg_destroy(H);
         return rc;
     }
+    // tabulated edge nodes for the levels smoothed by the single-block kernel
+    for (int l = 2; l <= levels && !rc; ++l) {
+        Lev& v = H->lev[l];
+        bool block = v.n + 1 <= H->small_max &&
+                     (H->fp32 ? block_smooth_smem<float>(v.n) : block_smooth_smem<double>(v.n)) <= (size_t)kBlockSmemMax;
+        if (block) rc = H->fp32 ? build_edge_table<float>(H, v, km, v.ef) : build_edge_table<double>(H, v, km, v.ed);
+    }
+    if (rc) {
+        mg_destroy(H);
+        return rc;
+    }
     // Coarse end of the cycle: with coarse_level d (default 5), a problem with
     // levels <= d runs whole cycles in the single-block kernel; a larger one
     // replaces the gamma coarse-grid steps on level d by a dense map computed
