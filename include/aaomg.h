@@ -163,6 +163,26 @@ AAOMG_API int mg_reset_profile(mg_handle h);
 /* Kernel launches issued by this handle since it was created (for reports). */
 AAOMG_API long long mg_kernel_launches(mg_handle h);
 
+/* r = f - A x and ||r||_{L^-1} / ||f||_{L^-1} (as mg_residual) WITHOUT a handle
+ * and without allocating any device memory.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate -- a program
+ * with a device memory budget fixed at start-up, a framework whose caching
+ * allocator owns all device memory, or a real-time loop that cannot afford the
+ * device synchronisation cudaMalloc/cudaFree may cause.  Its scratch (row
+ * partial sums) lives in a static device array of 4097 pairs of doubles
+ * (about 64 KB) that every device using the library keeps until exit.
+ *   levels:   1..12 (the finest grid, h = 2^-levels); 13 is rejected (BAD_ARG)
+ *             because its 8193 grid rows exceed the static scratch;
+ *   alpha > 0 and finite; k_variant 0 or 1 as in mg_options;
+ *   f, x: device pointers, 2N doubles each; r: device pointer or NULL;
+ *   relres: host pointer or NULL (if set, the call synchronises `stream`).
+ * The first call on a device looks up the scratch address on that device
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the scratch: calls that overlap on the GPU race and must be ordered by
+ * the caller.  Errors: BAD_ARG, NO_DEVICE, CUDA (no message is recorded). */
+AAOMG_API int mg_residual_noalloc(int levels, double alpha, int k_variant, const double* f, const double* x, double* r,
+                                  double* relres, void* stream);
+
 /* Name of an AAOMG_* code; message of the calling thread's last failure. */
 AAOMG_API const char* mg_strerror(int code);
 AAOMG_API const char* mg_last_error(void);

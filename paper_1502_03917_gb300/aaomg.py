@@ -86,6 +86,7 @@ def load():
             "mg_kernel_launches": (ctypes.c_longlong, [H]),
             "mg_get_profile": (I, [H, pD, ctypes.POINTER(ctypes.c_longlong)]),
             "mg_reset_profile": (I, [H]),
+            "mg_residual_noalloc": (I, [I, D, I, P, P, P, pD, P]),
             "mg_strerror": (ctypes.c_char_p, [I]),
             "mg_last_error": (ctypes.c_char_p, []),
         }
@@ -118,6 +119,19 @@ def _dptr(t, n=None):
     if n is not None and t.numel() != n:
         raise ValueError(f"expected {n} elements, got {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def residual_noalloc(levels: int, alpha: float, f, x, r=None, k_variant: int = 0):
+    """r = f - A x and the relative residual through mg_residual_noalloc: no
+    handle and no device allocation inside the library (its scratch is a static
+    device array; concurrent calls on different streams race)."""
+    lib = load()
+    N = ((1 << int(levels)) + 1) ** 2
+    rr = ctypes.c_double()
+    rp = _dptr(r, 2 * N) if r is not None else None
+    _check(lib.mg_residual_noalloc(int(levels), float(alpha), int(k_variant), _dptr(f, 2 * N), _dptr(x, 2 * N), rp,
+                                   ctypes.byref(rr), _stream()), "mg_residual_noalloc")
+    return rr.value
 
 
 class Solver:
