@@ -143,6 +143,20 @@ LevelP<T> make_params(int n, int ld, int64_t fs, double alpha, bool scaled, doub
         P.invNy_int = (T)(1.0 / Nd(2, 2, 0));
         P.invNl_int = (T)(1.0 / Nd(2, 2, 1));
     }
+    {
+        // columns of A at an interior node, scaled by the interior L^{-1}
+        double m[7], kd[7];
+        row_coeffs_general<double>(1, 1, n, h2, m, kd);
+        const double il = 1.0 / Ly(1, 1), ill = il / d;
+        const int rep[3] = {0, 1, 5};  // centre, E (edge), NE (diagonal)
+        for (int k = 0; k < 3; ++k) {
+            double mo = m[rep[k]], ko = c * (kd[rep[k]] + km * m[rep[k]]);
+            P.sc[0][k][0] = (T)(mo * il);   // y update: rh_y -= m p/L, rh_l -= cK p/L_l
+            P.sc[0][k][1] = (T)(ko * ill);
+            P.sc[1][k][0] = (T)(ko * il);   // lambda update: rh_y -= cK p/L, rh_l += m p/L
+            P.sc[1][k][1] = (T)(-mo * il);
+        }
+    }
     return P;
 }
 
@@ -201,8 +215,6 @@ struct mg_ctx {
     int nsm = 152;
     int band_min = 2049;      // levels with at least this many nodes per side use the one-launch LSGS step
     int small_max = 129;      // levels up to this many nodes per side: one launch per smoothing call
-    int csize = 1;            // cluster size of the one-launch smoothing kernel
-    bool use_cluster = false; // middle levels: one cluster launch instead of per-phase launches
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -285,15 +297,10 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* f = (T*)v.f;
     T* rh = (T*)v.rh;
     if (v.n + 1 <= H->small_max) {
-        // the whole smoothing call in one launch: one block when rh fits in
-        // shared memory, else one cluster over L2-resident data
+        // the whole smoothing call in one launch of one block when rh fits in
+        // shared memory
         if (block_smooth_smem<T>(v.n) <= (size_t)kBlockSmemMax) {
             launch_smooth_block<T>(P, etab<T>(v), H->o.smoother, steps, x, f, s);
-            H->rec_kernels += 1;
-            return;
-        }
-        if (H->csize >= 2 && H->use_cluster) {
-            launch_smooth_cluster<T>(P, H->o.smoother, steps, x, f, rh, H->csize, s);
             H->rec_kernels += 1;
             return;
         }
@@ -689,7 +696,6 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
             delete H;
             return fail(AAOMG_ERR_CUDA, std::string("smoothing kernel attributes: ") + cudaGetErrorString(e));
         }
-        H->csize = H->fp32 ? max_cluster_size<float>() : max_cluster_size<double>();
     }
     const double km = o.k_variant == 0 ? 1.0 : 0.0;
     {

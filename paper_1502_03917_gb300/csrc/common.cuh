@@ -49,6 +49,11 @@ struct LevelP {
     // stiffness stencil is 4 at the centre and -1 at E, W, N, S
     T mC, mO;
     T invLy_int, invNy_int, invNl_int;
+    // interior LSGS residual update: rh_o -= p * sc[field][k] (k = 0 centre,
+    // 1 E/W/N/S, 2 NE/SW), each a (y, lambda) pair of the column of A scaled by
+    // L^{-1}; mass and stiffness parts are combined here, which only rounds the
+    // smoother's carried residual (every defect is recomputed from x)
+    T sc[2][3][2];
     // boundary classes: node class cls3(i)+3*cls3(j) (9) and cls5(i)+5*cls5(j) (25)
     T invLy[9];
     T invNy[25];

@@ -22,7 +22,9 @@ namespace {
 
 // rh = L^{-1} (f - A x) on every node
 template <typename T>
-__global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ rh) {
+__global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ rhv) {
+    using V2 = typename P2<T>::t;
+    V2* rh = reinterpret_cast<V2*>(rhv);  // (y, lambda) pairs
     InteriorAll ia(P.n);
     EdgeNodes ed(P.n, -1);
     const int ni = ia.count(), nip = (ni + 31) & ~31;
@@ -33,13 +35,15 @@ __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __res
             resid_fast(P, f, x, rh, i, j);
         }
     } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
-        resid_hat_at(P, f, x, rh, i, j);
+        resid_hat_acc(P, f, x, RhPair<T>{rh}, i, j);
     }
 }
 
 // Algorithm 1 update: x += tau L^{-1} A rh (A symmetric), with rh = L^{-1} r
 template <typename T>
-__global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict__ rh) {
+__global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict__ rhv) {
+    using V2 = typename P2<T>::t;
+    V2* rh = reinterpret_cast<V2*>(const_cast<T*>(rhv));
     InteriorAll ia(P.n);
     EdgeNodes ed(P.n, -1);
     const int ni = ia.count(), nip = (ni + 31) & ~31;
@@ -50,7 +54,7 @@ __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict_
             ne_fast(P, x, rh, i, j);
         }
     } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
-        ne_update_at(P, x, rh, i, j);
+        ne_update_acc(P, x, RhPair<T>{rh}, i, j);
     }
 }
 
@@ -59,7 +63,9 @@ __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict_
 // rh_j -= A_ji p / L_jj on its neighbourhood.  Nodes of one colour share no
 // neighbour, so the updates of a phase are independent and race-free.
 template <typename T>
-__global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__ x, T* __restrict__ rh) {
+__global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__ x, T* __restrict__ rhv) {
+    using V2 = typename P2<T>::t;
+    V2* rh = reinterpret_cast<V2*>(rhv);
     InteriorColour ic(P.n, colour);
     EdgeNodes ed(P.n, colour);
     const int ni = ic.count(), nip = (ni + 31) & ~31;
@@ -67,7 +73,7 @@ __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__
     if (t < nip) {
         if (t < ni && ic.node(t, i, j)) lsgs_fast(P, field, x, rh, i, j);
     } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
-        lsgs_update_at(P, field, x, rh, i, j);
+        lsgs_update_acc(P, field, x, RhPair<T>{rh}, i, j);
     }
 }
 

@@ -61,99 +61,84 @@ struct EdgeNodes {
 };
 
 // ------------------------------------------------------- fast updates ----
-// Vectors in the layout of P (row stride P.ld, field stride P.fs); the node
-// (i,j) satisfies 2 <= i, j <= n-2.
+// The node (i,j) satisfies 2 <= i, j <= n-2.  x and f keep their two fields
+// apart (layout of P); the scaled residual rh is an array of (y, lambda) pairs
+// with row stride P.ld.  Pair arithmetic: the sums over the neighbours give
+// (M rh_y, M rh_l) and (Kd rh_y, Kd rh_l) at once.
 
-template <typename T>
-__device__ __forceinline__ void sums7(const T* v, int64_t p, int ld, T& s4, T& s6, T& v0) {
-    v0 = v[p];
-    s4 = (v[p + 1] + v[p - 1]) + (v[p + ld] + v[p - ld]);
-    s6 = s4 + (v[p + ld + 1] + v[p - ld - 1]);
+// (M v, Kd v) for both fields of a pair field v around linear index p
+template <typename V2>
+__device__ __forceinline__ void pair_stencil(const V2* v, int64_t p, int ld, V2 mC2, V2 mO2, V2& Mv, V2& Kv,
+                                             V2 (&nb)[7]) {
+    nb[0] = v[p];
+    nb[1] = v[p + 1];
+    nb[2] = v[p - 1];
+    nb[3] = v[p + ld];
+    nb[4] = v[p - ld];
+    nb[5] = v[p + ld + 1];
+    nb[6] = v[p - ld - 1];
+    V2 s4 = padd(padd(nb[1], nb[2]), padd(nb[3], nb[4]));
+    V2 s6 = padd(s4, padd(nb[5], nb[6]));
+    Mv = pfma(mC2, nb[0], pmul(mO2, s6));
+    using T = decltype(s4.x);
+    Kv = pfma(psplat(T(4)), nb[0], pmul(psplat(T(-1)), s4));
 }
 
 template <typename T>
-__device__ __forceinline__ void resid_fast(const LevelP<T>& P, const T* f, const T* x, T* rh, int i, int j) {
-    const int64_t p = (int64_t)j * P.ld + i;
-    T y0, y4, y6, l0, l4, l6;
-    sums7(x, p, P.ld, y4, y6, y0);
-    sums7(x + P.fs, p, P.ld, l4, l6, l0);
-    T My = P.mC * y0 + P.mO * y6, Ml = P.mC * l0 + P.mO * l6;
-    T Ky = T(4) * y0 - y4, Kl = T(4) * l0 - l4;
+__device__ __forceinline__ void resid_fast(const LevelP<T>& P, const T* f, const T* x,
+                                           typename P2<T>::t* __restrict__ rh, int i, int j) {
+    const int ld = P.ld;
+    const int64_t p = (int64_t)j * ld + i;
+    const T* xl = x + P.fs;
+    T y4 = (x[p + 1] + x[p - 1]) + (x[p + ld] + x[p - ld]);
+    T l4 = (xl[p + 1] + xl[p - 1]) + (xl[p + ld] + xl[p - ld]);
+    T y6 = y4 + (x[p + ld + 1] + x[p - ld - 1]);
+    T l6 = l4 + (xl[p + ld + 1] + xl[p - ld - 1]);
+    T My = P.mC * x[p] + P.mO * y6, Ml = P.mC * xl[p] + P.mO * l6;
+    T Ky = T(4) * x[p] - y4, Kl = T(4) * xl[p] - l4;
     T ay, al;
     rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
     const T il = P.invLy_int;
-    rh[p] = (f[p] - ay) * il;
-    rh[p + P.fs] = (f[p + P.fs] - al) * (il * P.invd);
+    rh[p] = pmake<T>((f[p] - ay) * il, (f[p + P.fs] - al) * (il * P.invd));
 }
 
 template <typename T>
-__device__ __forceinline__ void ne_fast(const LevelP<T>& P, T* x, const T* rh, int i, int j) {
+__device__ __forceinline__ void ne_fast(const LevelP<T>& P, T* x, const typename P2<T>::t* __restrict__ rh, int i,
+                                        int j) {
+    using V2 = typename P2<T>::t;
     const int64_t p = (int64_t)j * P.ld + i;
-    T y0, y4, y6, l0, l4, l6;
-    sums7(rh, p, P.ld, y4, y6, y0);
-    sums7(rh + P.fs, p, P.ld, l4, l6, l0);
-    T My = P.mC * y0 + P.mO * y6, Ml = P.mC * l0 + P.mO * l6;
-    T Ky = T(4) * y0 - y4, Kl = T(4) * l0 - l4;
+    V2 M, K, nb[7];
+    pair_stencil(rh, p, P.ld, psplat(P.mC), psplat(P.mO), M, K, nb);
     T qy, ql;
-    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
     const T il = P.invLy_int;
     x[p] += P.tau * il * qy;
     x[p + P.fs] += P.tau * (il * P.invd) * ql;
 }
 
 template <typename T>
-__device__ __forceinline__ void lsgs_fast(const LevelP<T>& P, int field, T* x, T* rh, int i, int j) {
+__device__ __forceinline__ void lsgs_fast(const LevelP<T>& P, int field, T* x, typename P2<T>::t* __restrict__ rh,
+                                          int i, int j) {
+    using V2 = typename P2<T>::t;
     const int ld = P.ld;
     const int64_t p = (int64_t)j * ld + i;
-    T* ry = rh;
-    T* rl = rh + P.fs;
-    const T r0 = ry[p], e = ry[p + 1], w = ry[p - 1], nn = ry[p + ld], so = ry[p - ld], ne = ry[p + ld + 1],
-            sw = ry[p - ld - 1];
-    const T l0 = rl[p], le = rl[p + 1], lw = rl[p - 1], ln = rl[p + ld], ls = rl[p - ld], lne = rl[p + ld + 1],
-            lsw = rl[p - ld - 1];
-    T y4 = (e + w) + (nn + so), l4 = (le + lw) + (ln + ls);
-    T My = P.mC * r0 + P.mO * (y4 + (ne + sw));
-    T Ml = P.mC * l0 + P.mO * (l4 + (lne + lsw));
-    T Ky = T(4) * r0 - y4, Kl = T(4) * l0 - l4;
+    V2 M, K, nb[7];
+    pair_stencil(rh, p, ld, psplat(P.mC), psplat(P.mO), M, K, nb);
     T qy, ql;
-    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
-    const T il = P.invLy_int, ill = P.invLy_int * P.invd;
-    T p_, dCy, dCl, dEy, dEl, dDy, dDl;
-    if (field == 0) {
-        p_ = qy * P.invNy_int;
-        x[p] += p_;
-        T mCp = P.mC * p_, mOp = P.mO * p_;
-        dCy = mCp * il;
-        dEy = mOp * il;
-        dDy = dEy;
-        dCl = P.c * (T(4) * p_ + P.km * mCp) * ill;
-        dEl = P.c * (-p_ + P.km * mOp) * ill;
-        dDl = P.c * (P.km * mOp) * ill;
-    } else {
-        p_ = ql * P.invNl_int;
-        x[p + P.fs] += p_;
-        T mCp = P.mC * p_, mOp = P.mO * p_;
-        dCy = P.c * (T(4) * p_ + P.km * mCp) * il;
-        dEy = P.c * (-p_ + P.km * mOp) * il;
-        dDy = P.c * (P.km * mOp) * il;
-        dCl = -mCp * il;
-        dEl = -mOp * il;
-        dDl = dEl;
-    }
-    ry[p] = r0 - dCy;
-    rl[p] = l0 - dCl;
-    ry[p + 1] = e - dEy;
-    rl[p + 1] = le - dEl;
-    ry[p - 1] = w - dEy;
-    rl[p - 1] = lw - dEl;
-    ry[p + ld] = nn - dEy;
-    rl[p + ld] = ln - dEl;
-    ry[p - ld] = so - dEy;
-    rl[p - ld] = ls - dEl;
-    ry[p + ld + 1] = ne - dDy;
-    rl[p + ld + 1] = lne - dDl;
-    ry[p - ld - 1] = sw - dDy;
-    rl[p - ld - 1] = lsw - dDl;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T pv = field == 0 ? qy * P.invNy_int : ql * P.invNl_int;
+    x[p + (field ? P.fs : 0)] += pv;
+    const V2 mp = psplat(-pv);
+    const V2 cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
+    const V2 cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
+    const V2 cD = pmake<T>(P.sc[field][2][0], P.sc[field][2][1]);
+    rh[p] = pfma(mp, cC, nb[0]);
+    rh[p + 1] = pfma(mp, cE, nb[1]);
+    rh[p - 1] = pfma(mp, cE, nb[2]);
+    rh[p + ld] = pfma(mp, cE, nb[3]);
+    rh[p - ld] = pfma(mp, cE, nb[4]);
+    rh[p + ld + 1] = pfma(mp, cD, nb[5]);
+    rh[p - ld - 1] = pfma(mp, cD, nb[6]);
 }
 
 }  // namespace aaomg

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include "band.h"
+#include "pair.cuh"
 #include "stencil.cuh"
 
 namespace aaomg {
@@ -143,65 +144,61 @@ __device__ void band_update_general(const LevelP<T>& P, const View<T, WT>& V, in
 // ------------------------------------------------------ interior fast path --
 // constant stencil: m = (mC; mO x6), kd = (4; -1 at E,W,N,S; 0 at NE,SW);
 // in the ring, column offsets are +-1 and row offsets select the slots sm/s/sp
+template <typename V2>
+__device__ __forceinline__ void ring_stencil(const V2* rs, const V2* rsp, const V2* rsm, int t, V2 mC2, V2 mO2,
+                                             V2& M, V2& K, V2 (&nb)[7]) {
+    nb[0] = rs[t];
+    nb[1] = rs[t + 1];
+    nb[2] = rs[t - 1];
+    nb[3] = rsp[t];
+    nb[4] = rsm[t];
+    nb[5] = rsp[t + 1];
+    nb[6] = rsm[t - 1];
+    V2 s4 = padd(padd(nb[1], nb[2]), padd(nb[3], nb[4]));
+    V2 s6 = padd(s4, padd(nb[5], nb[6]));
+    using T = decltype(s4.x);
+    M = pfma(mC2, nb[0], pmul(mO2, s6));
+    K = pfma(psplat(T(4)), nb[0], pmul(psplat(T(-1)), s4));
+}
+
 template <typename T, int WT>
 __device__ __forceinline__ void band_resid_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int t, int sxm, int sx,
                                                 int sxp, int sr, int sf) {
-    auto c0 = S->X[sx][t], e = S->X[sx][t + 1], w = S->X[sx][t - 1];
-    auto nn = S->X[sxp][t], so = S->X[sxm][t], ne = S->X[sxp][t + 1], sw = S->X[sxm][t - 1];
-    T s4y = (e.x + w.x) + (nn.x + so.x), s4l = (e.y + w.y) + (nn.y + so.y);
-    T My = P.mC * c0.x + P.mO * (s4y + (ne.x + sw.x));
-    T Ml = P.mC * c0.y + P.mO * (s4l + (ne.y + sw.y));
-    T Ky = T(4) * c0.x - s4y, Kl = T(4) * c0.y - s4l;
+    using V2 = typename V2<T>::type;
+    V2 M, K, nb[7];
+    ring_stencil(S->X[sx], S->X[sxp], S->X[sxm], t, psplat(P.mC), psplat(P.mO), M, K, nb);
     T ay, al;
-    rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
-    auto fv = S->F[sf][t];
+    rows_from_dots(P, M.x, K.x, M.y, K.y, ay, al);
+    const V2 fv = S->F[sf][t];
     const T il = P.invLy_int;
-    S->R[sr][t] = {(fv.x - ay) * il, (fv.y - al) * (il * P.invd)};
+    S->R[sr][t] = pmake<T>((fv.x - ay) * il, (fv.y - al) * (il * P.invd));
 }
 
 template <typename T, int WT>
 __device__ __forceinline__ void band_update_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int field, int t, int sm,
                                                  int s, int sp, int sx) {
-    auto r0 = S->R[s][t], e = S->R[s][t + 1], w = S->R[s][t - 1];
-    auto nn = S->R[sp][t], so = S->R[sm][t], ne = S->R[sp][t + 1], sw = S->R[sm][t - 1];
-    T s4y = (e.x + w.x) + (nn.x + so.x), s4l = (e.y + w.y) + (nn.y + so.y);
-    T My = P.mC * r0.x + P.mO * (s4y + (ne.x + sw.x));
-    T Ml = P.mC * r0.y + P.mO * (s4l + (ne.y + sw.y));
-    T Ky = T(4) * r0.x - s4y, Kl = T(4) * r0.y - s4l;
+    using V2 = typename V2<T>::type;
+    V2 M, K, nb[7];
+    V2* rs = S->R[s];
+    V2* rsp = S->R[sp];
+    V2* rsm = S->R[sm];
+    ring_stencil(rs, rsp, rsm, t, psplat(P.mC), psplat(P.mO), M, K, nb);
     T qy, ql;
-    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
-    const T il = P.invLy_int, ill = P.invLy_int * P.invd;
-    T p;
-    // per-offset increments of (rh_y, rh_lambda): centre, E/W/N/S, NE/SW
-    T dCy, dCl, dEy, dEl, dDy, dDl;
-    if (field == 0) {
-        p = qy * P.invNy_int;
-        S->X[sx][t].x += p;
-        T mCp = P.mC * p, mOp = P.mO * p;
-        dCy = mCp * il;
-        dEy = mOp * il;
-        dDy = dEy;
-        dCl = P.c * (T(4) * p + P.km * mCp) * ill;
-        dEl = P.c * (-p + P.km * mOp) * ill;
-        dDl = P.c * (P.km * mOp) * ill;
-    } else {
-        p = ql * P.invNl_int;
-        S->X[sx][t].y += p;
-        T mCp = P.mC * p, mOp = P.mO * p;
-        dCy = P.c * (T(4) * p + P.km * mCp) * il;
-        dEy = P.c * (-p + P.km * mOp) * il;
-        dDy = P.c * (P.km * mOp) * il;
-        dCl = -mCp * il;
-        dEl = -mOp * il;
-        dDl = dEl;
-    }
-    S->R[s][t] = {r0.x - dCy, r0.y - dCl};
-    S->R[s][t + 1] = {e.x - dEy, e.y - dEl};
-    S->R[s][t - 1] = {w.x - dEy, w.y - dEl};
-    S->R[sp][t] = {nn.x - dEy, nn.y - dEl};
-    S->R[sm][t] = {so.x - dEy, so.y - dEl};
-    S->R[sp][t + 1] = {ne.x - dDy, ne.y - dDl};
-    S->R[sm][t - 1] = {sw.x - dDy, sw.y - dDl};
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T pv = field == 0 ? qy * P.invNy_int : ql * P.invNl_int;
+    if (field == 0) S->X[sx][t].x += pv;
+    else S->X[sx][t].y += pv;
+    const V2 mp = psplat(-pv);
+    const V2 cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
+    const V2 cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
+    const V2 cD = pmake<T>(P.sc[field][2][0], P.sc[field][2][1]);
+    rs[t] = pfma(mp, cC, nb[0]);
+    rs[t + 1] = pfma(mp, cE, nb[1]);
+    rs[t - 1] = pfma(mp, cE, nb[2]);
+    rsp[t] = pfma(mp, cE, nb[3]);
+    rsm[t] = pfma(mp, cE, nb[4]);
+    rsp[t + 1] = pfma(mp, cD, nb[5]);
+    rsm[t - 1] = pfma(mp, cD, nb[6]);
 }
 
 template <typename T, int WT>
@@ -253,8 +250,9 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
     cp_async_wait<kPre - 1>();  // row jl has landed
     __syncthreads();
 
-    const int cm7 = ((c % 7) + 7) % 7;
-    int tm7 = jl % 7;
+    // phase index t* of the y update this column meets at step tau:
+    // t* = 5 (c + 2 tau + 6) mod 7, advancing by 3 (mod 7) per step
+    int ts = (5 * ((((c % 7) + 7) % 7 + 2 * (jl % 7) + 6) % 7)) % 7;
     for (int tau = jl; tau <= j1 - 1 + kLag; ++tau) {
         issue(tau + kPre);
         if (col_work) {
@@ -268,7 +266,6 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
                     band_resid_general<T, WT>(P, V, c, rho);
             }
             // the y phase and the lambda phase that meet this column at this step
-            const int ts = (5 * ((cm7 + 2 * tm7 + 6) % 7)) % 7;
             const int jy = tau - 4 - 2 * ts, jlam = jy - 14;
             if (jy >= jl && jy <= jh) {
                 if (col_fast && jy >= jfl && jy <= jfh)
@@ -292,7 +289,7 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
                 xout[g + P.fs] = v.y;
             }
         }
-        tm7 = tm7 == 6 ? 0 : tm7 + 1;
+        ts = ts >= 4 ? ts - 4 : ts + 3;
         cp_async_wait<kPre - 1>();  // row tau + 1 has landed
         __syncthreads();
     }

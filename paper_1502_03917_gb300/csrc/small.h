@@ -1,4 +1,4 @@
-// small.h -- one-launch smoothing calls for small and middle levels (internal).
+// small.h -- one-launch smoothing calls for small levels (internal).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -21,16 +21,9 @@ size_t block_smooth_smem(int n);
 template <typename T>
 cudaError_t small_prepare();
 // `steps` smoothing steps (smoother 0 NE, 1 LSGS, 2 sLSGS) on one level in one
-// launch: one thread block (rh in shared memory) ...
+// launch of one thread block (rh in shared memory)
 template <typename T>
 void launch_smooth_block(const LevelP<T>& P, const EdgeTable<T>& E, int smoother, int steps, T* x, const T* f,
                          cudaStream_t s);
-// ... or one cluster of `csize` blocks (x, f, rh in global memory / L2)
-template <typename T>
-cudaError_t launch_smooth_cluster(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, T* rh, int csize,
-                                  cudaStream_t s);
-// largest cluster size (16, 8, ...) the device can schedule for that kernel
-template <typename T>
-int max_cluster_size();
 
 }  // namespace aaomg

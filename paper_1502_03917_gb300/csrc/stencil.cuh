@@ -6,6 +6,7 @@
 // global memory and on shared memory.
 #pragma once
 #include "common.cuh"
+#include "pair.cuh"
 
 namespace aaomg {
 
@@ -108,22 +109,58 @@ __device__ __forceinline__ void apply_A(const LevelP<T>& P, const T* x, int i, i
     rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
 }
 
-// rh = L^{-1}(f - A x) at node (i,j)
+// The scaled residual rh = L^{-1}(f - A x) is addressed through an accessor:
+// RhSep keeps the two fields apart (field stride fs), RhPair interleaves them.
 template <typename T>
-__device__ __forceinline__ void resid_hat_at(const LevelP<T>& P, const T* f, const T* x, T* rh, int i, int j) {
+struct RhSep {
+    T* r;
+    int64_t fs;
+    __device__ __forceinline__ T& y(int64_t p) const { return r[p]; }
+    __device__ __forceinline__ T& l(int64_t p) const { return r[p + fs]; }
+};
+template <typename T>
+struct RhPair {
+    typename P2<T>::t* r;
+    __device__ __forceinline__ T& y(int64_t p) const { return r[p].x; }
+    __device__ __forceinline__ T& l(int64_t p) const { return r[p].y; }
+};
+
+// rh at the 7 offsets of node (i,j) for both fields; 0 where the offset leaves the grid
+template <typename T, typename R>
+__device__ __forceinline__ void load7_rh(const LevelP<T>& P, const R& rh, int i, int j, T ry[7], T rl[7]) {
+    const bool in = node_interior(P, i, j);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        int ii = i + DI(o), jj = j + DJ(o);
+        bool ok = in || in_grid(ii, jj, P.n);
+        int64_t q = ok ? nidx(P, ii, jj) : 0;
+        ry[o] = ok ? rh.y(q) : T(0);
+        rl[o] = ok ? rh.l(q) : T(0);
+    }
+}
+
+// rh = L^{-1}(f - A x) at node (i,j)
+template <typename T, typename R>
+__device__ __forceinline__ void resid_hat_acc(const LevelP<T>& P, const T* f, const T* x, const R& rh, int i, int j) {
     T ay, al;
     apply_A(P, x, i, j, ay, al);
     int64_t p = nidx(P, i, j);
     T il = inv_ly(P, i, j);
-    rh[p] = (f[p] - ay) * il;
-    rh[p + P.fs] = (f[p + P.fs] - al) * (il * P.invd);
+    rh.y(p) = (f[p] - ay) * il;
+    rh.l(p) = (f[p + P.fs] - al) * (il * P.invd);
 }
 
 // Algorithm 1 update at node (i,j): x += tau L^{-1} A rh (A symmetric)
-template <typename T>
-__device__ __forceinline__ void ne_update_at(const LevelP<T>& P, T* x, const T* rh, int i, int j) {
-    T qy, ql;
-    apply_A(P, rh, i, j, qy, ql);
+template <typename T, typename R>
+__device__ __forceinline__ void ne_update_acc(const LevelP<T>& P, T* x, const R& rh, int i, int j) {
+    T m[7], kd[7], ry[7], rl[7];
+    row_coeffs(P, i, j, m, kd);
+    load7_rh(P, rh, i, j, ry, rl);
+    bool in = node_interior(P, i, j);
+    T My, Ky, Ml, Kl, qy, ql;
+    dots(in, m, kd, ry, My, Ky);
+    dots(in, m, kd, rl, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
     int64_t p = nidx(P, i, j);
     T il = inv_ly(P, i, j);
     x[p] += P.tau * il * qy;
@@ -132,12 +169,11 @@ __device__ __forceinline__ void ne_update_at(const LevelP<T>& P, T* x, const T* 
 
 // Algorithm 2 update of unknown (field, node (i,j)): q = sum_j A_ij rh_j,
 // p = q / N_ii, x_i += p, rh_j -= A_ji p / L_jj over the neighbourhood.
-template <typename T>
-__device__ __forceinline__ void lsgs_update_at(const LevelP<T>& P, int field, T* x, T* rh, int i, int j) {
+template <typename T, typename R>
+__device__ __forceinline__ void lsgs_update_acc(const LevelP<T>& P, int field, T* x, const R& rh, int i, int j) {
     T m[7], kd[7], ry[7], rl[7];
     row_coeffs(P, i, j, m, kd);
-    load7(P, rh, i, j, ry);
-    load7(P, rh + P.fs, i, j, rl);
+    load7_rh(P, rh, i, j, ry, rl);
     bool in = node_interior(P, i, j);
     T My, Ky, Ml, Kl;
     dots(in, m, kd, ry, My, Ky);
@@ -156,13 +192,27 @@ __device__ __forceinline__ void lsgs_update_at(const LevelP<T>& P, int field, T*
         T mp = m[o] * p;
         T kp = P.c * (kd[o] * p + P.km * mp);
         if (field == 0) {
-            rh[q] = ry[o] - mp * il;
-            rh[q + P.fs] = rl[o] - kp * (il * P.invd);
+            rh.y(q) = ry[o] - mp * il;
+            rh.l(q) = rl[o] - kp * (il * P.invd);
         } else {
-            rh[q] = ry[o] - kp * il;
-            rh[q + P.fs] = rl[o] + mp * il;
+            rh.y(q) = ry[o] - kp * il;
+            rh.l(q) = rl[o] + mp * il;
         }
     }
+}
+
+// the same with the two fields of rh apart (field stride P.fs)
+template <typename T>
+__device__ __forceinline__ void resid_hat_at(const LevelP<T>& P, const T* f, const T* x, T* rh, int i, int j) {
+    resid_hat_acc(P, f, x, RhSep<T>{rh, P.fs}, i, j);
+}
+template <typename T>
+__device__ __forceinline__ void ne_update_at(const LevelP<T>& P, T* x, const T* rh, int i, int j) {
+    ne_update_acc(P, x, RhSep<T>{const_cast<T*>(rh), P.fs}, i, j);
+}
+template <typename T>
+__device__ __forceinline__ void lsgs_update_at(const LevelP<T>& P, int field, T* x, T* rh, int i, int j) {
+    lsgs_update_acc(P, field, x, RhSep<T>{rh, P.fs}, i, j);
 }
 
 // defect restricted to coarse node (I,J): P^T (f - A x), weight 1 at (2I,2J)
