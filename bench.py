@@ -191,7 +191,16 @@ def run_ours(args, rank, world, local):
             its[a] = it
 
         def step():
-            run_all(one)
+            if args.serial:
+                run_all(one)
+                return
+            # all alphas in flight at once through the library's batch call
+            for a in ALPHAS:
+                xs[a].zero_()
+            it, rr, code = mg.solve_batch([solvers[a] for a in ALPHAS], [fs[a] for a in ALPHAS],
+                                          [xs[a] for a in ALPHAS], tol=args.tol)
+            for a, k in zip(ALPHAS, it):
+                its[a] = k
 
         for _ in range(W):
             step()

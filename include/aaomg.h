@@ -149,6 +149,30 @@ AAOMG_API int mg_solve(mg_handle h, const double* f, double* x, double tol, int*
 AAOMG_API int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol, int* iters, double* relres,
                   void* stream);
 
+/* Independent problems in one call: handles[k] solves A_k x_k = f_k from the
+ * initial guess in x_k (device pointers) to `tol`, all instances in flight at
+ * once (each on a stream of its own handle, ordered after the work already on
+ * `stream`; `stream` waits for all of them).  iters / relres (NULL or arrays of
+ * count) receive each instance's result.  The handles must be distinct.
+ * Returns the first nonzero status of an instance, else AAOMG_OK. */
+AAOMG_API int mg_solve_batch(int count, const mg_handle* handles, const double* const* f, double* const* x, double tol,
+                             int* iters, double* relres, void* stream);
+
+/* The control u = alpha^{-1} lambda (eq. (mp2) and the relation below it) of
+ * x = (y, lambda): x 2N doubles, u N doubles, device pointers. */
+AAOMG_API int mg_control(mg_handle h, const double* x, double* u, void* stream);
+
+/* Adjoint of the solve for a loss L(u) of the control u = lambda / alpha.
+ * Given the solution x = (y, lambda) of A x = (M y_D, 0) and ubar = dL/du
+ * (N doubles), solves A z = (0, ubar / alpha) to `tol` (A is symmetric, so the
+ * adjoint operator is A itself) and returns
+ *   gyD     = dL/dy_D  = M z_y                                   (N doubles),
+ *   *dalpha = dL/dalpha = -alpha^{-2} (ubar . lambda + z_lambda^T M lambda),
+ * the second term from dA/dalpha = [[0,0],[0,alpha^{-2} M]].  z (2N doubles)
+ * receives the adjoint state.  Device pointers except dalpha (host). */
+AAOMG_API int mg_adjoint(mg_handle h, const double* x, const double* ubar, double* z, double* gyD, double* dalpha,
+                         double tol, void* stream);
+
 /* Relative residual after each iteration of the last mg_solve: buf[0] is the
  * initial one; *n receives the count written (<= cap). */
 AAOMG_API int mg_get_history(mg_handle h, double* buf, int cap, int* n);

@@ -87,6 +87,9 @@ def load():
             "mg_get_profile": (I, [H, pD, ctypes.POINTER(ctypes.c_longlong)]),
             "mg_reset_profile": (I, [H]),
             "mg_residual_noalloc": (I, [I, D, I, P, P, P, pD, P]),
+            "mg_solve_batch": (I, [I, ctypes.POINTER(H), ctypes.POINTER(P), ctypes.POINTER(P), D, pI, pD, P]),
+            "mg_control": (I, [H, P, P, P]),
+            "mg_adjoint": (I, [H, P, P, P, P, pD, D, P]),
             "mg_strerror": (ctypes.c_char_p, [I]),
             "mg_last_error": (ctypes.c_char_p, []),
         }
@@ -132,6 +135,22 @@ def residual_noalloc(levels: int, alpha: float, f, x, r=None, k_variant: int = 0
     _check(lib.mg_residual_noalloc(int(levels), float(alpha), int(k_variant), _dptr(f, 2 * N), _dptr(x, 2 * N), rp,
                                    ctypes.byref(rr), _stream()), "mg_residual_noalloc")
     return rr.value
+
+
+def solve_batch(solvers, fs, xs, tol: float = 1e-8, raise_on_fail: bool = True):
+    """Solve independent problems at once (mg_solve_batch): solvers[k] on
+    (fs[k], xs[k]); returns (iterations, relative residuals, status)."""
+    lib = load()
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s._h for s in solvers])
+    fp = (ctypes.c_void_p * n)(*[_dptr(f, 2 * s.N) for s, f in zip(solvers, fs)])
+    xp = (ctypes.c_void_p * n)(*[_dptr(x, 2 * s.N) for s, x in zip(solvers, xs)])
+    it = (ctypes.c_int * n)()
+    rr = (ctypes.c_double * n)()
+    code = lib.mg_solve_batch(n, hs, fp, xp, float(tol), it, rr, _stream())
+    if raise_on_fail:
+        _check(code, "mg_solve_batch")
+    return list(it), list(rr), code
 
 
 class Solver:
@@ -230,6 +249,26 @@ class Solver:
         if raise_on_fail:
             _check(code, "mg_solve_host")
         return it.value, rr.value, code
+
+    def control(self, x, u=None):
+        """u = lambda / alpha of x = (y, lambda)."""
+        import torch
+
+        u = torch.empty(self.N, dtype=torch.float64, device=x.device) if u is None else u
+        _check(self._lib.mg_control(self._h, _dptr(x, 2 * self.N), _dptr(u, self.N), _stream()), "mg_control")
+        return u
+
+    def adjoint(self, x, ubar, tol: float = 1e-10):
+        """(gyD, dL/dalpha, z) for a loss of the control u = lambda/alpha, given
+        the solution x and ubar = dL/du (see mg_adjoint)."""
+        import torch
+
+        z = torch.empty(2 * self.N, dtype=torch.float64, device=x.device)
+        gyD = torch.empty(self.N, dtype=torch.float64, device=x.device)
+        da = ctypes.c_double()
+        _check(self._lib.mg_adjoint(self._h, _dptr(x, 2 * self.N), _dptr(ubar, self.N), _dptr(z, 2 * self.N),
+                                    _dptr(gyD, self.N), ctypes.byref(da), float(tol), _stream()), "mg_adjoint")
+        return gyD, da.value, z
 
     def history(self):
         buf = (ctypes.c_double * 1024)()

@@ -231,6 +231,8 @@ struct mg_ctx {
     double* red = nullptr;    // reduced norms (device)
     double* h_red = nullptr;  // pinned host copy
     cudaStream_t cap = nullptr;
+    cudaStream_t own = nullptr;   // the handle's stream for mg_solve_batch
+    cudaEvent_t norms_ready = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long graph_kernels = 0;
@@ -549,19 +551,6 @@ int collect_profile(mg_ctx* H) {
     return AAOMG_OK;
 }
 
-// residual of the FP64 iterate; in FP32 mode also writes the scaled FP32 defect
-// into the inner finest right-hand side.  Leaves norms in H->h_red after sync.
-int residual_norms(mg_ctx* H, cudaStream_t s, bool write_inner) {
-    Lev& v = H->lev[H->L];
-    float* fin = (H->fp32 && write_inner) ? (float*)v.f : nullptr;
-    launch_resid64(H->fine64, iter_f(H), iter_x(H), nullptr, fin, v.ld, v.fs, H->part, kResidBlocks, H->red, s);
-    H->launches += 2;
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(H->h_red, H->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return collect_profile(H);
-}
-
 int run_iteration(mg_ctx* H, cudaStream_t s) {
     CK(cudaGraphLaunch(H->gexec, s));
     H->launches += H->graph_kernels;
@@ -578,35 +567,69 @@ int check_handle(mg_handle h) {
 
 int64_t vec_bytes(mg_ctx* H) { return (int64_t)2 * H->fine64.fs * (int64_t)sizeof(double); }
 
-// solve loop on the internal FP64 copies
-int solve_internal(mg_ctx* H, double tol, int* iters, double* relres, cudaStream_t s) {
-    H->hist.clear();
+// The solve loop on the internal FP64 copies, as a state machine so that many
+// handles can be driven at once: begin() queues the first residual and its
+// norms; after that work has finished, step() reads the norms, decides, and
+// queues the next iteration and residual.
+struct SolveState {
     int it = 0;
-    double rr = 0.0, r0 = 0.0;
+    double r0 = 0.0, rr = 0.0;
     int status = AAOMG_OK;
-    for (;;) {
-        int rc = residual_norms(H, s, true);
-        if (rc) return rc;
-        double fn = H->h_red[1] > 0.0 ? H->h_red[1] : 1.0;
-        rr = std::sqrt(H->h_red[0] / fn);
-        H->hist.push_back(rr);
-        if (it == 0) r0 = rr;
-        if (!std::isfinite(rr) || rr > 1e6 * (r0 > 0 ? r0 : 1.0)) {
-            status = fail(AAOMG_ERR_DIVERGED, "residual diverged");
-            break;
-        }
-        if (rr <= tol) break;
-        if (it >= H->o.max_iter) {
-            status = fail(AAOMG_ERR_NOT_CONVERGED, "max_iter reached");
-            break;
-        }
-        rc = run_iteration(H, s);
-        if (rc) return rc;
-        ++it;
+};
+
+int queue_norms(mg_ctx* H, cudaStream_t s) {
+    Lev& v = H->lev[H->L];
+    float* fin = H->fp32 ? (float*)v.f : nullptr;
+    launch_resid64(H->fine64, iter_f(H), iter_x(H), nullptr, fin, v.ld, v.fs, H->part, kResidBlocks, H->red, s);
+    H->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(H->h_red, H->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(H->norms_ready, s));
+    return AAOMG_OK;
+}
+
+int solve_begin(mg_ctx* H, cudaStream_t s) {
+    H->hist.clear();
+    return queue_norms(H, s);
+}
+
+// after norms_ready: returns 1 when the solve is over (status in st), 0 if an
+// iteration was queued, < 0 on a CUDA error
+int solve_step(mg_ctx* H, double tol, SolveState& st, cudaStream_t s) {
+    int rc = collect_profile(H);
+    if (rc) return rc;
+    double fn = H->h_red[1] > 0.0 ? H->h_red[1] : 1.0;
+    st.rr = std::sqrt(H->h_red[0] / fn);
+    H->hist.push_back(st.rr);
+    if (st.it == 0) st.r0 = st.rr;
+    if (!std::isfinite(st.rr) || st.rr > 1e6 * (st.r0 > 0 ? st.r0 : 1.0)) {
+        st.status = fail(AAOMG_ERR_DIVERGED, "residual diverged");
+        return 1;
     }
-    if (iters) *iters = it;
-    if (relres) *relres = rr;
-    return status;
+    if (st.rr <= tol) return 1;
+    if (st.it >= H->o.max_iter) {
+        st.status = fail(AAOMG_ERR_NOT_CONVERGED, "max_iter reached");
+        return 1;
+    }
+    if ((rc = run_iteration(H, s))) return rc;
+    ++st.it;
+    if ((rc = queue_norms(H, s))) return rc;
+    return 0;
+}
+
+int solve_internal(mg_ctx* H, double tol, int* iters, double* relres, cudaStream_t s) {
+    SolveState st;
+    int rc = solve_begin(H, s);
+    if (rc) return rc;
+    for (;;) {
+        CK(cudaEventSynchronize(H->norms_ready));
+        rc = solve_step(H, tol, st, s);
+        if (rc < 0) return rc;
+        if (rc == 1) break;
+    }
+    if (iters) *iters = st.it;
+    if (relres) *relres = st.rr;
+    return st.status;
 }
 
 // copy the caller's (FP64, paper's scaling) vector into the FP32 finest level
@@ -642,6 +665,8 @@ void mg_destroy(mg_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->own) cudaStreamDestroy(h->own);
+    if (h->norms_ready) cudaEventDestroy(h->norms_ready);
     for (void* p : h->allocs) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
     delete h;
@@ -796,6 +821,11 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     if ((rc = build_graph(H))) {
         mg_destroy(H);
         return rc;
+    }
+    if (cudaStreamCreateWithFlags(&H->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&H->norms_ready, cudaEventDisableTiming) != cudaSuccess) {
+        mg_destroy(H);
+        return fail(AAOMG_ERR_CUDA, "stream or event creation");
     }
     *out = H;
     return AAOMG_OK;
@@ -958,6 +988,92 @@ int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol,
     if (status == AAOMG_ERR_CUDA) return status;
     CK(cudaMemcpyAsync(x_host, iter_x(h), bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    return status;
+}
+
+int mg_solve_batch(int count, const mg_handle* handles, const double* const* f, double* const* x, double tol,
+                   int* iters, double* relres, void* stream) {
+    if (count < 0 || (count > 0 && (!handles || !f || !x)) || !(tol >= 0.0))
+        return fail(AAOMG_ERR_BAD_ARG, "bad batch arguments");
+    for (int k = 0; k < count; ++k) {
+        if (!handles[k] || !f[k] || !x[k]) return fail(AAOMG_ERR_BAD_ARG, "null handle or vector in batch");
+        for (int q = 0; q < k; ++q)
+            if (handles[q] == handles[k]) return fail(AAOMG_ERR_BAD_ARG, "a handle appears twice in the batch");
+    }
+    if (count == 0) return AAOMG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = check_handle(handles[0]);
+    if (rc) return rc;
+    cudaEvent_t start = nullptr;
+    CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    CK(cudaEventRecord(start, s));
+    std::vector<SolveState> st(count);
+    std::vector<char> active(count, 1);
+    int status = AAOMG_OK;
+    for (int k = 0; k < count; ++k) {
+        mg_ctx* H = handles[k];
+        size_t bytes = (size_t)vec_bytes(H);
+        CK(cudaStreamWaitEvent(H->own, start, 0));
+        CK(cudaMemcpyAsync(iter_f(H), f[k], bytes, cudaMemcpyDeviceToDevice, H->own));
+        CK(cudaMemcpyAsync(iter_x(H), x[k], bytes, cudaMemcpyDeviceToDevice, H->own));
+        if ((rc = solve_begin(H, H->own))) return rc;
+    }
+    int left = count;
+    while (left > 0) {
+        for (int k = 0; k < count; ++k) {
+            if (!active[k]) continue;
+            mg_ctx* H = handles[k];
+            CK(cudaEventSynchronize(H->norms_ready));
+            rc = solve_step(H, tol, st[k], H->own);
+            if (rc < 0) return rc;
+            if (rc == 1) {
+                active[k] = 0;
+                --left;
+                CK(cudaMemcpyAsync(x[k], iter_x(H), (size_t)vec_bytes(H), cudaMemcpyDeviceToDevice, H->own));
+                CK(cudaEventRecord(H->norms_ready, H->own));
+                CK(cudaStreamWaitEvent(s, H->norms_ready, 0));
+                if (iters) iters[k] = st[k].it;
+                if (relres) relres[k] = st[k].rr;
+                if (st[k].status != AAOMG_OK && status == AAOMG_OK) status = st[k].status;
+            }
+        }
+    }
+    cudaEventDestroy(start);
+    return status;
+}
+
+int mg_control(mg_handle h, const double* x, double* u, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x || !u) return fail(AAOMG_ERR_BAD_ARG, "null vector");
+    launch_control(h->fine64.fs, x, h->alpha, u, (cudaStream_t)stream);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int mg_adjoint(mg_handle h, const double* x, const double* ubar, double* z, double* gyD, double* dalpha, double tol,
+               void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x || !ubar || !z || !gyD || !dalpha || !(tol >= 0.0)) return fail(AAOMG_ERR_BAD_ARG, "null vector or bad tol");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nn = h->fine64.fs;
+    // adjoint right-hand side into the internal right-hand side, z from zero
+    launch_adjoint_rhs(nn, ubar, h->alpha, iter_f(h), s);
+    CK(cudaMemsetAsync(iter_x(h), 0, (size_t)vec_bytes(h), s));
+    h->launches += 1;
+    int it = 0;
+    double rr = 0.0;
+    int status = solve_internal(h, tol, &it, &rr, s);
+    if (status == AAOMG_ERR_CUDA) return status;
+    CK(cudaMemcpyAsync(z, iter_x(h), (size_t)vec_bytes(h), cudaMemcpyDeviceToDevice, s));
+    launch_adjoint_terms(h->fine64, x, ubar, z, gyD, h->part, kResidBlocks, h->red, s);
+    h->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_red, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *dalpha = -(h->h_red[0] + h->h_red[1]) / (h->alpha * h->alpha);
     return status;
 }
 

@@ -369,3 +369,65 @@ template void launch_dense_apply<float>(const float*, int, const float*, float*,
 template void launch_dense_apply<double>(const double*, int, const double*, double*, cudaStream_t);
 
 }  // namespace aaomg
+
+// ------------------------------------------------------------- adjoint --
+namespace aaomg {
+namespace {
+
+// u = lambda / alpha
+__global__ void k_control(int64_t nn, const double* __restrict__ x, double invalpha, double* __restrict__ u) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x)
+        u[t] = x[nn + t] * invalpha;
+}
+
+// g = (0, ubar / alpha)
+__global__ void k_adjoint_rhs(int64_t nn, const double* __restrict__ ubar, double invalpha, double* __restrict__ g) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        g[t] = 0.0;
+        g[nn + t] = ubar[t] * invalpha;
+    }
+}
+
+// gyD = M z_y, and per-block partials of ubar . lambda and (M z_lambda) . lambda
+__global__ void k_adjoint_terms(LevelP<double> P, const double* __restrict__ x, const double* __restrict__ ubar,
+                                const double* __restrict__ z, double* __restrict__ gyD, double* __restrict__ part) {
+    const int64_t nn = (int64_t)(P.n + 1) * (P.n + 1);
+    double a = 0.0, b = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(t / (P.n + 1)), i = (int)(t - (int64_t)j * (P.n + 1));
+        double m[7], kd[7], zy[7], zl[7];
+        row_coeffs(P, i, j, m, kd);
+        load7(P, z, i, j, zy);
+        load7(P, z + P.fs, i, j, zl);
+        double mzy = 0.0, mzl = 0.0;
+        for (int o = 0; o < 7; ++o) {
+            mzy += m[o] * zy[o];
+            mzl += m[o] * zl[o];
+        }
+        gyD[t] = mzy;
+        double lam = x[nn + t];
+        a += ubar[t] * lam;
+        b += mzl * lam;
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+}  // namespace
+
+void launch_control(int64_t nn, const double* x, double alpha, double* u, cudaStream_t s) {
+    k_control<<<608, 256, 0, s>>>(nn, x, 1.0 / alpha, u);
+}
+void launch_adjoint_rhs(int64_t nn, const double* ubar, double alpha, double* g, cudaStream_t s) {
+    k_adjoint_rhs<<<608, 256, 0, s>>>(nn, ubar, 1.0 / alpha, g);
+}
+void launch_adjoint_terms(const LevelP<double>& P, const double* x, const double* ubar, const double* z, double* gyD,
+                          double* part, int nblk, double* out, cudaStream_t s) {
+    k_adjoint_terms<<<nblk, 256, 0, s>>>(P, x, ubar, z, gyD, part);
+    k_reduce_parts<<<1, 256, 0, s>>>(part, nblk, out);
+}
+
+}  // namespace aaomg

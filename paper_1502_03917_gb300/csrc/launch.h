@@ -31,6 +31,12 @@ void launch_to_f64(int n, const float* v, int64_t v_ld, int64_t v_fs, double* ou
                    double s_l, cudaStream_t s);
 void launch_rhs(const LevelP<double>& P, const double* yD, double* f, cudaStream_t s);
 
+void launch_control(int64_t nn, const double* x, double alpha, double* u, cudaStream_t s);
+void launch_adjoint_rhs(int64_t nn, const double* ubar, double alpha, double* g, cudaStream_t s);
+// gyD = M z_y; out[0] = ubar . lambda, out[1] = (M z_lambda) . lambda (device)
+void launch_adjoint_terms(const LevelP<double>& P, const double* x, const double* ubar, const double* z, double* gyD,
+                          double* part, int nblk, double* out, cudaStream_t s);
+
 constexpr int kResidBlocks = 304;  // 2 x 152 SMs
 
 }  // namespace aaomg
