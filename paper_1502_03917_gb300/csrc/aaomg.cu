@@ -298,7 +298,7 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* x = (T*)v.x;
     T* f = (T*)v.f;
     T* rh = (T*)v.rh;
-    if (v.n + 1 <= H->small_max) {
+    if (v.n + 1 <= H->small_max && v.n <= 128) {
         // the whole smoothing call in one launch of one block when rh fits in
         // shared memory
         if (block_smooth_smem<T>(v.n) <= (size_t)kBlockSmemMax) {
@@ -760,7 +760,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     // tabulated edge nodes for the levels smoothed by the single-block kernel
     for (int l = 2; l <= levels && !rc; ++l) {
         Lev& v = H->lev[l];
-        bool block = v.n + 1 <= H->small_max &&
+        bool block = v.n + 1 <= H->small_max && v.n <= 128 &&
                      (H->fp32 ? block_smooth_smem<float>(v.n) : block_smooth_smem<double>(v.n)) <= (size_t)kBlockSmemMax;
         if (block) rc = H->fp32 ? build_edge_table<float>(H, v, km, v.ef) : build_edge_table<double>(H, v, km, v.ed);
     }

@@ -21,18 +21,21 @@ namespace {
 // constant-stencil path with the general one.
 
 // rh = L^{-1} (f - A x) on every node
-template <typename T>
+// N > 0: kernel instantiated for n = N cells (strides are compile-time
+// constants); N = 0: any n
+template <typename T, int N>
 __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ rhv) {
     using V2 = typename P2<T>::t;
     V2* rh = reinterpret_cast<V2*>(rhv);  // (y, lambda) pairs
-    InteriorAll ia(P.n);
-    EdgeNodes ed(P.n, -1);
+    const int n = N > 0 ? N : P.n, ld = n + 1, fs = ld * ld;
+    InteriorAll ia(n);
+    EdgeNodes ed(n, -1);
     const int ni = ia.count(), nip = (ni + 31) & ~31;
     int t = blockIdx.x * blockDim.x + threadIdx.x, i, j;
     if (t < nip) {
         if (t < ni) {
             ia.node(t, i, j);
-            resid_fast(P, f, x, rh, i, j);
+            resid_fast(P, f, x, rh, i, j, ld, fs);
         }
     } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
         resid_hat_acc(P, f, x, RhPair<T>{rh}, i, j);
@@ -40,18 +43,19 @@ __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __res
 }
 
 // Algorithm 1 update: x += tau L^{-1} A rh (A symmetric), with rh = L^{-1} r
-template <typename T>
+template <typename T, int N>
 __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict__ rhv) {
     using V2 = typename P2<T>::t;
     V2* rh = reinterpret_cast<V2*>(const_cast<T*>(rhv));
-    InteriorAll ia(P.n);
-    EdgeNodes ed(P.n, -1);
+    const int n = N > 0 ? N : P.n, ld = n + 1, fs = ld * ld;
+    InteriorAll ia(n);
+    EdgeNodes ed(n, -1);
     const int ni = ia.count(), nip = (ni + 31) & ~31;
     int t = blockIdx.x * blockDim.x + threadIdx.x, i, j;
     if (t < nip) {
         if (t < ni) {
             ia.node(t, i, j);
-            ne_fast(P, x, rh, i, j);
+            ne_fast(P, x, rh, i, j, ld, fs);
         }
     } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
         ne_update_acc(P, x, RhPair<T>{rh}, i, j);
@@ -62,16 +66,17 @@ __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict_
 // colour `colour` does q = sum_j A_ij rh_j, p = q / N_ii, x_i += p and
 // rh_j -= A_ji p / L_jj on its neighbourhood.  Nodes of one colour share no
 // neighbour, so the updates of a phase are independent and race-free.
-template <typename T>
+template <typename T, int N>
 __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__ x, T* __restrict__ rhv) {
     using V2 = typename P2<T>::t;
     V2* rh = reinterpret_cast<V2*>(rhv);
-    InteriorColour ic(P.n, colour);
-    EdgeNodes ed(P.n, colour);
+    const int n = N > 0 ? N : P.n, ld = n + 1, fs = ld * ld;
+    InteriorColour ic(n, colour);
+    EdgeNodes ed(n, colour);
     const int ni = ic.count(), nip = (ni + 31) & ~31;
     int t = blockIdx.x * blockDim.x + threadIdx.x, i, j;
     if (t < nip) {
-        if (t < ni && ic.node(t, i, j)) lsgs_fast(P, field, x, rh, i, j);
+        if (t < ni && ic.node(t, i, j)) lsgs_fast(P, field, x, rh, i, j, ld, fs);
     } else if (t - nip < ed.count() && ed.node(t - nip, i, j)) {
         lsgs_update_acc(P, field, x, RhPair<T>{rh}, i, j);
     }
@@ -265,20 +270,35 @@ inline int split_threads(int n, bool colour) {
     int ne = rows * full + (n >= 4 ? 4 * (n - 3) : 0);
     return ((ni + 31) & ~31) + ne;
 }
+// instantiate the level kernels for the grid sizes of the middle levels
+#define AAOMG_BY_N(N_, CALL)                  \
+    switch (N_) {                             \
+    case 128: CALL(128); break;               \
+    case 256: CALL(256); break;               \
+    case 512: CALL(512); break;               \
+    case 1024: CALL(1024); break;             \
+    default: CALL(0); break;                  \
+    }
 template <typename T>
 void launch_resid_hat(const LevelP<T>& P, const T* f, const T* x, T* rh, cudaStream_t s) {
-    int nt = split_threads(P.n, false);
-    k_resid_hat<T><<<(nt + 255) / 256, 256, 0, s>>>(P, f, x, rh);
+    int nb = (split_threads(P.n, false) + 255) / 256;
+#define L_(N) k_resid_hat<T, N><<<nb, 256, 0, s>>>(P, f, x, rh)
+    AAOMG_BY_N(P.n, L_)
+#undef L_
 }
 template <typename T>
 void launch_ne_update(const LevelP<T>& P, T* x, const T* rh, cudaStream_t s) {
-    int nt = split_threads(P.n, false);
-    k_ne_update<T><<<(nt + 255) / 256, 256, 0, s>>>(P, x, rh);
+    int nb = (split_threads(P.n, false) + 255) / 256;
+#define L_(N) k_ne_update<T, N><<<nb, 256, 0, s>>>(P, x, rh)
+    AAOMG_BY_N(P.n, L_)
+#undef L_
 }
 template <typename T>
 void launch_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, T* rh, cudaStream_t s) {
-    int nt = split_threads(P.n, true);
-    k_lsgs_phase<T><<<(nt + 255) / 256, 256, 0, s>>>(P, field, colour, x, rh);
+    int nb = (split_threads(P.n, true) + 255) / 256;
+#define L_(N) k_lsgs_phase<T, N><<<nb, 256, 0, s>>>(P, field, colour, x, rh)
+    AAOMG_BY_N(P.n, L_)
+#undef L_
 }
 template <typename T>
 void launch_restrict(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* f, const T* x, T* fc, T* xc, cudaStream_t s) {

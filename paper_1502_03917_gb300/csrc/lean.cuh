@@ -68,7 +68,7 @@ struct EdgeNodes {
 
 // (M v, Kd v) for both fields of a pair field v around linear index p
 template <typename V2>
-__device__ __forceinline__ void pair_stencil(const V2* v, int64_t p, int ld, V2 mC2, V2 mO2, V2& Mv, V2& Kv,
+__device__ __forceinline__ void pair_stencil(const V2* v, int p, int ld, V2 mC2, V2 mO2, V2& Mv, V2& Kv,
                                              V2 (&nb)[7]) {
     nb[0] = v[p];
     nb[1] = v[p + 1];
@@ -84,12 +84,13 @@ __device__ __forceinline__ void pair_stencil(const V2* v, int64_t p, int ld, V2 
     Kv = pfma(psplat(T(4)), nb[0], pmul(psplat(T(-1)), s4));
 }
 
+// `ld` and `fs` are the row and field strides (compile-time constants in the
+// kernels instantiated per level size)
 template <typename T>
 __device__ __forceinline__ void resid_fast(const LevelP<T>& P, const T* f, const T* x,
-                                           typename P2<T>::t* __restrict__ rh, int i, int j) {
-    const int ld = P.ld;
-    const int64_t p = (int64_t)j * ld + i;
-    const T* xl = x + P.fs;
+                                           typename P2<T>::t* __restrict__ rh, int i, int j, int ld, int fs) {
+    const int p = j * ld + i;
+    const T* xl = x + fs;
     T y4 = (x[p + 1] + x[p - 1]) + (x[p + ld] + x[p - ld]);
     T l4 = (xl[p + 1] + xl[p - 1]) + (xl[p + ld] + xl[p - ld]);
     T y6 = y4 + (x[p + ld + 1] + x[p - ld - 1]);
@@ -99,35 +100,34 @@ __device__ __forceinline__ void resid_fast(const LevelP<T>& P, const T* f, const
     T ay, al;
     rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
     const T il = P.invLy_int;
-    rh[p] = pmake<T>((f[p] - ay) * il, (f[p + P.fs] - al) * (il * P.invd));
+    rh[p] = pmake<T>((f[p] - ay) * il, (f[p + fs] - al) * (il * P.invd));
 }
 
 template <typename T>
 __device__ __forceinline__ void ne_fast(const LevelP<T>& P, T* x, const typename P2<T>::t* __restrict__ rh, int i,
-                                        int j) {
+                                        int j, int ld, int fs) {
     using V2 = typename P2<T>::t;
-    const int64_t p = (int64_t)j * P.ld + i;
+    const int p = j * ld + i;
     V2 M, K, nb[7];
-    pair_stencil(rh, p, P.ld, psplat(P.mC), psplat(P.mO), M, K, nb);
+    pair_stencil(rh, p, ld, psplat(P.mC), psplat(P.mO), M, K, nb);
     T qy, ql;
     rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
     const T il = P.invLy_int;
     x[p] += P.tau * il * qy;
-    x[p + P.fs] += P.tau * (il * P.invd) * ql;
+    x[p + fs] += P.tau * (il * P.invd) * ql;
 }
 
 template <typename T>
 __device__ __forceinline__ void lsgs_fast(const LevelP<T>& P, int field, T* x, typename P2<T>::t* __restrict__ rh,
-                                          int i, int j) {
+                                          int i, int j, int ld, int fs) {
     using V2 = typename P2<T>::t;
-    const int ld = P.ld;
-    const int64_t p = (int64_t)j * ld + i;
+    const int p = j * ld + i;
     V2 M, K, nb[7];
     pair_stencil(rh, p, ld, psplat(P.mC), psplat(P.mO), M, K, nb);
     T qy, ql;
     rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
     const T pv = field == 0 ? qy * P.invNy_int : ql * P.invNl_int;
-    x[p + (field ? P.fs : 0)] += pv;
+    x[p + (field ? fs : 0)] += pv;
     const V2 mp = psplat(-pv);
     const V2 cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
     const V2 cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
