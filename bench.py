@@ -50,6 +50,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-vcycle", action="store_true", help="skip the V-cycle comparison")
+    p.add_argument("--profiling-run", action="store_true",
+                   help="for runs under an external profiler: no CUDA events inside the solver graphs and no "
+                        "nvidia-smi sampling (roofline and clocks are then not reported)")
     p.add_argument("--serial", action="store_true",
                    help="solve the alphas one after another instead of concurrently on separate streams")
     return p.parse_args()
@@ -211,8 +215,9 @@ def run_ours(args, rank, world, local):
         if world > 1:
             torch.distributed.barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        clk = ClockSampler(local)
-        clk.start()
+        clk = ClockSampler(local if not args.profiling_run else -1)
+        if not args.profiling_run:
+            clk.start()
         for k in range(K):
             flush.fill_(float(k))
             ev[k][0].record()
@@ -238,7 +243,7 @@ def run_ours(args, rank, world, local):
     N = ((1 << L) + 1) ** 2
     unknowns_step = len(ALPHAS) * 2 * N
 
-    sol32 = make("fp32_refine", True)
+    sol32 = make("fp32_refine", not args.profiling_run)
     ms, its32, launches, prof, clocks, xs32 = timed_steps(sol32, K, W)
     ms = max_over_ranks(ms)
     value = world * unknowns_step * K / (ms / 1e3)
@@ -284,6 +289,17 @@ def run_ours(args, rank, world, local):
                              "iterations": {str(a): its64[a] for a in ALPHAS},
                              "max_rel_diff_fp32refine_vs_fp64": err}
         for s in sol64.values():
+            s.close()
+
+    if not args.no_vcycle and args.cycle == "W":
+        # the same workload with the V-cycle (one coarse-grid step per level)
+        solv = {a: mg.Solver(L, a, smoother=args.smoother, precision="fp32_refine", cycle="V", max_iter=100)
+                for a in ALPHAS}
+        msv, itsv, _, _, _, _ = timed_steps(solv, max(1, min(K, 2)), 1)
+        msv = max_over_ranks(msv)
+        out["vcycle"] = {"value": world * unknowns_step * max(1, min(K, 2)) / (msv / 1e3),
+                         "ms_per_step": msv / max(1, min(K, 2)), "iterations": {str(a): itsv[a] for a in ALPHAS}}
+        for s in solv.values():
             s.close()
 
     if not args.no_e2e:
