@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-vcycle", action="store_true", help="skip the V-cycle comparison")
+    p.add_argument("--inner-cycles", type=int, default=0, help="FP32 cycles per refinement step (0: library default)")
     p.add_argument("--profiling-run", action="store_true",
                    help="for runs under an external profiler: no CUDA events inside the solver graphs and no "
                         "nvidia-smi sampling (roofline and clocks are then not reported)")
@@ -147,7 +148,7 @@ def run_ours(args, rank, world, local):
 
     def make(precision, profile):
         return {a: mg.Solver(L, a, smoother=args.smoother, precision=precision, cycle=args.cycle, max_iter=100,
-                             profile=profile) for a in ALPHAS}
+                             profile=profile, inner_cycles=args.inner_cycles) for a in ALPHAS}
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 

@@ -13,7 +13,9 @@
 // step touch a common unknown or residual entry, so a step needs one barrier.
 // Within a colour the updates commute exactly (each residual entry receives one
 // update per phase), so the result equals the sequential multicolour sweep.
-// Each column meets exactly one y phase and one lambda phase per step.
+// Each column meets exactly one y phase and one lambda phase per step; two
+// threads share a column (half 0: prefetch and y update; half 1: residual,
+// lambda update and output).
 //
 // Halos.  The final iterate at node (i,j) depends only on the initial data in
 // columns i-28..i+15 and rows j-28..j+15, so a block computes columns
@@ -202,11 +204,14 @@ __device__ __forceinline__ void band_update_fast(const LevelP<T>& P, BandSmem<T,
 }
 
 template <typename T, int WT>
-__global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ xin,
-                                                  T* __restrict__ xout, int W, int Hs) {
+__global__ void __launch_bounds__(2 * WT) k_lsgs_band(LevelP<T> P, const T* __restrict__ f,
+                                                      const T* __restrict__ xin, T* __restrict__ xout, int W, int Hs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BandSmem<T, WT>* S = reinterpret_cast<BandSmem<T, WT>*>(smem_raw);
-    const int tid = threadIdx.x;
+    // two threads per column: half 0 prefetches and does the y update, half 1
+    // forms the residual, does the lambda update and writes the output
+    const int tid = threadIdx.x % WT;
+    const int half = threadIdx.x / WT;
     const int i0 = blockIdx.x * W;
     const int i1 = min(i0 + W, P.n + 1);
     const int c0 = i0 - kBandHL;
@@ -226,9 +231,12 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
     const int jfl = max(2, jl + 1), jfh = min(P.n - 2, jh - 1);  // rows whose neighbourhood is fast
 
     using V2T = typename V2<T>::type;
-    for (int r = 0; r < kRing; ++r) S->X[r][tid] = V2T{T(0), T(0)};
-    for (int r = 0; r < kRRing; ++r) S->R[r][tid] = V2T{T(0), T(0)};
-    for (int r = 0; r < kFRing; ++r) S->F[r][tid] = V2T{T(0), T(0)};
+    if (half == 0) {
+        for (int r = 0; r < kRing; ++r) S->X[r][tid] = V2T{T(0), T(0)};
+    } else {
+        for (int r = 0; r < kRRing; ++r) S->R[r][tid] = V2T{T(0), T(0)};
+        for (int r = 0; r < kFRing; ++r) S->F[r][tid] = V2T{T(0), T(0)};
+    }
     __syncthreads();
 
     // one commit group per row, also for rows outside the window
@@ -246,16 +254,27 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
         }
         cp_async_commit();
     };
-    for (int row = jl; row < jl + kPre; ++row) issue(row);
-    cp_async_wait<kPre - 1>();  // row jl has landed
+    if (half == 0) {
+        for (int row = jl; row < jl + kPre; ++row) issue(row);
+        cp_async_wait<kPre - 1>();  // row jl has landed
+    }
     __syncthreads();
 
     // phase index t* of the y update this column meets at step tau:
     // t* = 5 (c + 2 tau + 6) mod 7, advancing by 3 (mod 7) per step
     int ts = (5 * ((((c % 7) + 7) % 7 + 2 * (jl % 7) + 6) % 7)) % 7;
     for (int tau = jl; tau <= j1 - 1 + kLag; ++tau) {
-        issue(tau + kPre);
-        if (col_work) {
+        const int jy = tau - 4 - 2 * ts, jlam = jy - 14;
+        if (half == 0) {
+            issue(tau + kPre);
+            if (col_work && jy >= jl && jy <= jh) {
+                if (col_fast && jy >= jfl && jy <= jfh)
+                    band_update_fast<T, WT>(P, S, 0, tid, (jy - 1) & (kRRing - 1), jy & (kRRing - 1),
+                                            (jy + 1) & (kRRing - 1), jy & (kRing - 1));
+                else
+                    band_update_general<T, WT>(P, V, 0, c, jy);
+            }
+        } else if (col_work) {
             // rh of row rho = tau - 2 from the original iterate
             const int rho = tau - 2;
             if (rho >= jl && rho <= jh) {
@@ -265,15 +284,7 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
                 else
                     band_resid_general<T, WT>(P, V, c, rho);
             }
-            // the y phase and the lambda phase that meet this column at this step
-            const int jy = tau - 4 - 2 * ts, jlam = jy - 14;
-            if (jy >= jl && jy <= jh) {
-                if (col_fast && jy >= jfl && jy <= jfh)
-                    band_update_fast<T, WT>(P, S, 0, tid, (jy - 1) & (kRRing - 1), jy & (kRRing - 1),
-                                            (jy + 1) & (kRRing - 1), jy & (kRing - 1));
-                else
-                    band_update_general<T, WT>(P, V, 0, c, jy);
-            }
+            // the lambda phase that meets this column at this step
             if (jlam >= jl && jlam <= jh) {
                 if (col_fast && jlam >= jfl && jlam <= jfh)
                     band_update_fast<T, WT>(P, S, 1, tid, (jlam - 1) & (kRRing - 1), jlam & (kRRing - 1),
@@ -290,10 +301,10 @@ __global__ void __launch_bounds__(WT) k_lsgs_band(LevelP<T> P, const T* __restri
             }
         }
         ts = ts >= 4 ? ts - 4 : ts + 3;
-        cp_async_wait<kPre - 1>();  // row tau + 1 has landed
+        if (half == 0) cp_async_wait<kPre - 1>();  // row tau + 1 has landed
         __syncthreads();
     }
-    cp_async_wait<0>();
+    if (half == 0) cp_async_wait<0>();
 }
 
 }  // namespace
@@ -312,7 +323,7 @@ cudaError_t band_prepare() {
 template <typename T>
 void launch_lsgs_band(const LevelP<T>& P, const T* f, const T* xin, T* xout, const BandGrid& g, cudaStream_t s) {
     constexpr int WT = band_threads<T>();
-    k_lsgs_band<T, WT><<<dim3(g.nb, g.ns), WT, band_smem_bytes<T>(), s>>>(P, f, xin, xout, g.W, g.Hs);
+    k_lsgs_band<T, WT><<<dim3(g.nb, g.ns), 2 * WT, band_smem_bytes<T>(), s>>>(P, f, xin, xout, g.W, g.Hs);
 }
 
 template size_t band_smem_bytes<float>();
