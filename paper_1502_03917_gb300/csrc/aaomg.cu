@@ -13,6 +13,7 @@
 
 #include "aaomg.h"
 #include "band.h"
+#include "cluster.h"
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
@@ -43,7 +44,9 @@ struct Lev {
     void* f = nullptr;
     void* rh = nullptr;
     BandGrid bg{};
-    EdgeTable<float> ef{};   // tabulated edge nodes for the single-block smoothing kernel
+    bool block = false;      // smoothing calls in one launch of one block
+    int cs = 0;              // > 0: smoothing calls in one launch of a cluster of cs blocks
+    EdgeTable<float> ef{};   // tabulated edge nodes for the one-launch smoothing kernels
     EdgeTable<double> ed{};
     LevelP<float> pf{};
     LevelP<double> pd{};
@@ -214,7 +217,7 @@ struct mg_ctx {
     int dev = 0;
     int nsm = 152;
     int band_min = 2049;      // levels with at least this many nodes per side use the one-launch LSGS step
-    int small_max = 129;      // levels up to this many nodes per side: one launch per smoothing call
+    int small_max = 257;      // levels up to this many nodes per side: one launch per smoothing call
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -298,14 +301,18 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* x = (T*)v.x;
     T* f = (T*)v.f;
     T* rh = (T*)v.rh;
-    if (v.n + 1 <= H->small_max && v.n <= 128) {
-        // the whole smoothing call in one launch of one block when rh fits in
-        // shared memory
-        if (block_smooth_smem<T>(v.n) <= (size_t)kBlockSmemMax) {
-            launch_smooth_block<T>(P, etab<T>(v), H->o.smoother, steps, x, f, s);
-            H->rec_kernels += 1;
-            return;
-        }
+    if (v.cs > 0) {
+        // the whole smoothing call in one launch of one cluster (x and rh in
+        // the blocks' shared memory)
+        launch_smooth_cluster<T>(P, H->o.smoother, steps, x, f, v.cs, s);
+        H->rec_kernels += 1;
+        return;
+    }
+    if (v.block) {
+        // the whole smoothing call in one launch of one block (rh in shared memory)
+        launch_smooth_block<T>(P, etab<T>(v), H->o.smoother, steps, x, f, s);
+        H->rec_kernels += 1;
+        return;
     }
     switch (H->o.smoother) {
     case MG_SMOOTHER_NE:
@@ -416,6 +423,15 @@ int record_iteration(mg_ctx* H, cudaStream_t s) {
 }
 
 // Tabulated edge nodes of level v (see edge.h), in the cycle's precision.
+// blocks per cluster of the one-launch smoothing call by level size and
+// precision (measured on GB300): 0 keeps the single-block kernel, which wins on
+// 65 x 65 nodes in FP32
+int default_cluster(int n, bool fp32) {
+    if (n <= 64) return fp32 ? 0 : 8;
+    if (n <= 128) return fp32 ? 8 : 16;
+    return 16;
+}
+
 template <typename T>
 int build_edge_table(mg_ctx* H, Lev& v, double km, EdgeTable<T>& E) {
     const int n = v.n;
@@ -717,6 +733,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     }
     {
         cudaError_t e = H->fp32 ? small_prepare<float>() : small_prepare<double>();
+        if (e == cudaSuccess) e = H->fp32 ? cluster_prepare<float>() : cluster_prepare<double>();
         if (e != cudaSuccess) {
             delete H;
             return fail(AAOMG_ERR_CUDA, std::string("smoothing kernel attributes: ") + cudaGetErrorString(e));
@@ -757,12 +774,31 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         mg_destroy(H);
         return rc;
     }
-    // tabulated edge nodes for the levels smoothed by the single-block kernel
+    // One-launch smoothing calls on the levels with at most small_max nodes per
+    // side: a cluster of blocks on the mid-size levels (with the cluster size
+    // cluster_size, else one by level size), a single block on the small ones.
     for (int l = 2; l <= levels && !rc; ++l) {
         Lev& v = H->lev[l];
-        bool block = v.n + 1 <= H->small_max && v.n <= 128 &&
-                     (H->fp32 ? block_smooth_smem<float>(v.n) : block_smooth_smem<double>(v.n)) <= (size_t)kBlockSmemMax;
-        if (block) rc = H->fp32 ? build_edge_table<float>(H, v, km, v.ef) : build_edge_table<double>(H, v, km, v.ed);
+        if (v.n + 1 > H->small_max) continue;
+        if (cluster_level(v.n) && o.cluster_size != 1) {
+            auto runs = [&](int cs) {
+                return (H->fp32 ? cluster_max_active<float>(v.n, cs) : cluster_max_active<double>(v.n, cs)) > 0;
+            };
+            if (o.cluster_size > 1) {
+                if (runs(o.cluster_size)) v.cs = o.cluster_size;
+                else
+                    rc = fail(AAOMG_ERR_BAD_ARG, "cluster_size " + std::to_string(o.cluster_size) +
+                                                     " cannot run on a level with " + std::to_string(v.n + 1) +
+                                                     " nodes per side");
+            } else {
+                for (int cs = default_cluster(v.n, H->fp32); cs >= 2 && !v.cs; cs /= 2)
+                    if (runs(cs)) v.cs = cs;
+            }
+        }
+        v.block = !v.cs && v.n <= 128 &&
+                  (H->fp32 ? block_smooth_smem<float>(v.n) : block_smooth_smem<double>(v.n)) <= (size_t)kBlockSmemMax;
+        if (!rc && v.block)
+            rc = H->fp32 ? build_edge_table<float>(H, v, km, v.ef) : build_edge_table<double>(H, v, km, v.ed);
     }
     if (rc) {
         mg_destroy(H);

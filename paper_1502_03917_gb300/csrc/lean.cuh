@@ -141,4 +141,78 @@ __device__ __forceinline__ void lsgs_fast(const LevelP<T>& P, int field, T* x, t
     rh[p - ld - 1] = pfma(mp, cD, nb[6]);
 }
 
+// ------------------------------------------------ row-pointer variants ----
+// The same updates with the three rows j-1, j, j+1 of a pair field given as
+// separate pointers (rows of a ring buffer, or rows that live in the shared
+// memory of another block of a cluster); i is the index within the row.
+
+template <typename V2>
+__device__ __forceinline__ void rows_stencil(const V2* rs, const V2* rsp, const V2* rsm, int i, V2 mC2, V2 mO2,
+                                             V2& M, V2& K, V2 (&nb)[7]) {
+    nb[0] = rs[i];
+    nb[1] = rs[i + 1];
+    nb[2] = rs[i - 1];
+    nb[3] = rsp[i];
+    nb[4] = rsm[i];
+    nb[5] = rsp[i + 1];
+    nb[6] = rsm[i - 1];
+    V2 s4 = padd(padd(nb[1], nb[2]), padd(nb[3], nb[4]));
+    V2 s6 = padd(s4, padd(nb[5], nb[6]));
+    using T = decltype(s4.x);
+    M = pfma(mC2, nb[0], pmul(mO2, s6));
+    K = pfma(psplat(T(4)), nb[0], pmul(psplat(T(-1)), s4));
+}
+
+// rh pair L^{-1}(f - A x) of a node from the x rows and its (f_y, f_lambda)
+template <typename T, typename V2>
+__device__ __forceinline__ V2 rows_resid_fast(const LevelP<T>& P, const V2* xs, const V2* xsp, const V2* xsm, int i,
+                                              T fy, T fl) {
+    V2 M, K, nb[7];
+    rows_stencil(xs, xsp, xsm, i, psplat(P.mC), psplat(P.mO), M, K, nb);
+    T ay, al;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, ay, al);
+    const T il = P.invLy_int;
+    return pmake<T>((fy - ay) * il, (fl - al) * (il * P.invd));
+}
+
+// Algorithm 1 update of the x pair xr[i] from the rh rows
+template <typename T, typename V2>
+__device__ __forceinline__ void rows_ne_fast(const LevelP<T>& P, V2* xr, const V2* rs, const V2* rsp, const V2* rsm,
+                                             int i) {
+    V2 M, K, nb[7];
+    rows_stencil(rs, rsp, rsm, i, psplat(P.mC), psplat(P.mO), M, K, nb);
+    T qy, ql;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T il = P.invLy_int;
+    V2 v = xr[i];
+    v.x += P.tau * il * qy;
+    v.y += P.tau * (il * P.invd) * ql;
+    xr[i] = v;
+}
+
+// Algorithm 2 update of one field of the x pair xr[i], with the scatter into
+// the rh rows
+template <typename T, typename V2>
+__device__ __forceinline__ void rows_lsgs_fast(const LevelP<T>& P, int field, V2* xr, V2* rs, V2* rsp, V2* rsm,
+                                               int i) {
+    V2 M, K, nb[7];
+    rows_stencil(rs, rsp, rsm, i, psplat(P.mC), psplat(P.mO), M, K, nb);
+    T qy, ql;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T pv = field == 0 ? qy * P.invNy_int : ql * P.invNl_int;
+    if (field == 0) xr[i].x += pv;
+    else xr[i].y += pv;
+    const V2 mp = psplat(-pv);
+    const V2 cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
+    const V2 cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
+    const V2 cD = pmake<T>(P.sc[field][2][0], P.sc[field][2][1]);
+    rs[i] = pfma(mp, cC, nb[0]);
+    rs[i + 1] = pfma(mp, cE, nb[1]);
+    rs[i - 1] = pfma(mp, cE, nb[2]);
+    rsp[i] = pfma(mp, cE, nb[3]);
+    rsm[i] = pfma(mp, cE, nb[4]);
+    rsp[i + 1] = pfma(mp, cD, nb[5]);
+    rsm[i - 1] = pfma(mp, cD, nb[6]);
+}
+
 }  // namespace aaomg

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "band.h"
+#include "lean.cuh"
 #include "pair.cuh"
 #include "stencil.cuh"
 
@@ -144,63 +145,18 @@ __device__ void band_update_general(const LevelP<T>& P, const View<T, WT>& V, in
 }
 
 // ------------------------------------------------------ interior fast path --
-// constant stencil: m = (mC; mO x6), kd = (4; -1 at E,W,N,S; 0 at NE,SW);
-// in the ring, column offsets are +-1 and row offsets select the slots sm/s/sp
-template <typename V2>
-__device__ __forceinline__ void ring_stencil(const V2* rs, const V2* rsp, const V2* rsm, int t, V2 mC2, V2 mO2,
-                                             V2& M, V2& K, V2 (&nb)[7]) {
-    nb[0] = rs[t];
-    nb[1] = rs[t + 1];
-    nb[2] = rs[t - 1];
-    nb[3] = rsp[t];
-    nb[4] = rsm[t];
-    nb[5] = rsp[t + 1];
-    nb[6] = rsm[t - 1];
-    V2 s4 = padd(padd(nb[1], nb[2]), padd(nb[3], nb[4]));
-    V2 s6 = padd(s4, padd(nb[5], nb[6]));
-    using T = decltype(s4.x);
-    M = pfma(mC2, nb[0], pmul(mO2, s6));
-    K = pfma(psplat(T(4)), nb[0], pmul(psplat(T(-1)), s4));
-}
-
+// constant stencil (lean.cuh); in the ring, row offsets select the slots sm/s/sp
 template <typename T, int WT>
 __device__ __forceinline__ void band_resid_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int t, int sxm, int sx,
                                                 int sxp, int sr, int sf) {
-    using V2 = typename V2<T>::type;
-    V2 M, K, nb[7];
-    ring_stencil(S->X[sx], S->X[sxp], S->X[sxm], t, psplat(P.mC), psplat(P.mO), M, K, nb);
-    T ay, al;
-    rows_from_dots(P, M.x, K.x, M.y, K.y, ay, al);
-    const V2 fv = S->F[sf][t];
-    const T il = P.invLy_int;
-    S->R[sr][t] = pmake<T>((fv.x - ay) * il, (fv.y - al) * (il * P.invd));
+    const typename V2<T>::type fv = S->F[sf][t];
+    S->R[sr][t] = rows_resid_fast<T>(P, S->X[sx], S->X[sxp], S->X[sxm], t, fv.x, fv.y);
 }
 
 template <typename T, int WT>
 __device__ __forceinline__ void band_update_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int field, int t, int sm,
                                                  int s, int sp, int sx) {
-    using V2 = typename V2<T>::type;
-    V2 M, K, nb[7];
-    V2* rs = S->R[s];
-    V2* rsp = S->R[sp];
-    V2* rsm = S->R[sm];
-    ring_stencil(rs, rsp, rsm, t, psplat(P.mC), psplat(P.mO), M, K, nb);
-    T qy, ql;
-    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
-    const T pv = field == 0 ? qy * P.invNy_int : ql * P.invNl_int;
-    if (field == 0) S->X[sx][t].x += pv;
-    else S->X[sx][t].y += pv;
-    const V2 mp = psplat(-pv);
-    const V2 cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
-    const V2 cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
-    const V2 cD = pmake<T>(P.sc[field][2][0], P.sc[field][2][1]);
-    rs[t] = pfma(mp, cC, nb[0]);
-    rs[t + 1] = pfma(mp, cE, nb[1]);
-    rs[t - 1] = pfma(mp, cE, nb[2]);
-    rsp[t] = pfma(mp, cE, nb[3]);
-    rsm[t] = pfma(mp, cE, nb[4]);
-    rsp[t + 1] = pfma(mp, cD, nb[5]);
-    rsm[t - 1] = pfma(mp, cD, nb[6]);
+    rows_lsgs_fast<T>(P, field, S->X[sx], S->R[s], S->R[sp], S->R[sm], t);
 }
 
 template <typename T, int WT>

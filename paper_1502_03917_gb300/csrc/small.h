@@ -14,6 +14,8 @@ constexpr int small_threads() {
     return sizeof(T) == 4 ? 1024 : 512;
 }
 constexpr int kBlockSmemMax = 227 * 1024;
+// dynamic shared memory of the cluster kernel (it also has a small static table)
+constexpr int kClusterSmemMax = kBlockSmemMax - 8 * 1024;
 
 // shared memory of the single-block kernel for a level with n cells
 template <typename T>

@@ -1,0 +1,392 @@
+// smooth_cluster.cu -- a whole smoothing call (nu steps of Algorithm 1 or 2) on
+// one mid-size level (65 to 257 nodes per side) in ONE launch of ONE
+// thread-block cluster.
+//
+// On these levels a colour phase of Algorithm 2 has a few hundred to a few
+// thousand independent updates: too few to fill the GPU, too many for one
+// block to finish quickly, and a launch per phase costs more than the phase.
+// Here the level's grid rows are split into cs strips, one per block of a
+// cluster (cs = 4 to 16 SMs).  Each block keeps the iterate x and the scaled
+// residual rh = L^{-1}(f - Ax) of its strip in its own shared memory as
+// (y, lambda) pairs for the whole call; x is read from global memory once at
+// the start and written back once at the end.  A node in the first or last row
+// of a strip reaches one row into the neighbouring strip: those loads and, for
+// Algorithm 2, the residual updates of the scatter go to the neighbouring
+// block's shared memory (distributed shared memory).  The phases are separated
+// by cluster barriers (release / acquire), which also make those remote stores
+// visible.  Within a colour phase no two updates touch a common unknown or
+// residual entry (distance-2 colouring), so the result is the sequential
+// multicolour sweep's whatever the strips.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "cluster.h"
+#include "lean.cuh"
+#include "small.h"
+#include "stencil.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace aaomg {
+
+namespace {
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n\t"
+        "barrier.cluster.wait.acquire.aligned;\n" ::
+            : "memory");
+}
+
+// The strip of this block: own rows [r0, r1) in shared memory, and the
+// boundary rows of the neighbouring strips (null at the grid's bottom / top).
+template <typename T, int N>
+struct Strip {
+    using V2 = typename P2<T>::t;
+    static constexpr int LD = N + 1;
+    int r0, r1;
+    V2 *X, *R;    // own rows
+    V2 *Xb, *Rb;  // row r0 - 1 (last row of the block below)
+    V2 *Xa, *Ra;  // row r1 (first row of the block above)
+    // rows j in [r0 - 1, r1]
+    __device__ __forceinline__ V2* xrow(int j) const { return j < r0 ? Xb : (j >= r1 ? Xa : X + (j - r0) * LD); }
+    __device__ __forceinline__ V2* rrow(int j) const { return j < r0 ? Rb : (j >= r1 ? Ra : R + (j - r0) * LD); }
+};
+
+// ------------------------------------------------------- edge nodes --
+// Nodes within two rows or columns of the boundary.  Their stencils, the L_y^-1
+// of their neighbours and their N_ii^-1 depend only on the node's boundary
+// class cls5(i) + 5 cls5(j); each block tabulates the 25 classes in shared
+// memory at the start (no global-memory latency inside a phase).
+template <typename T>
+struct EdgeClass {
+    T m[7], kd[7], il[7];  // il: L_y^-1 of neighbour o (0 outside the grid)
+    T iny, inl;            // N_ii^-1 of the two fields
+};
+
+template <typename T, int N>
+__device__ void edge_class_init(const LevelP<T>& P, int k, EdgeClass<T>& C) {
+    // a representative node of each class: 0, 1, 2, N-1, N
+    auto rep = [](int a) { return a <= 2 ? a : N - 4 + a; };
+    const int i = rep(k % 5), j = rep(k / 5);
+    row_coeffs_general<T>(i, j, N, P.h2, C.m, C.kd);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        const int ii = i + DI(o), jj = j + DJ(o);
+        C.il[o] = in_grid(ii, jj, N) ? inv_ly(P, ii, jj) : T(0);
+    }
+    C.iny = inv_n(P, 0, i, j);
+    C.inl = inv_n(P, 1, i, j);
+}
+
+template <typename T, int N, typename RowPtr, typename V2>
+__device__ __forceinline__ void cl_gather(const RowPtr (&rows)[3], int i, int j, const EdgeClass<T>& C, V2 (&v)[7],
+                                          T& My, T& Ky, T& Ml, T& Kl) {
+    My = Ky = Ml = Kl = T(0);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        const int ii = i + DI(o), jj = j + DJ(o);
+        v[o] = in_grid(ii, jj, N) ? rows[DJ(o) + 1][ii] : pmake<T>(T(0), T(0));
+        My += C.m[o] * v[o].x;
+        Ky += C.kd[o] * v[o].x;
+        Ml += C.m[o] * v[o].y;
+        Kl += C.kd[o] * v[o].y;
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void cl_resid_edge(const LevelP<T>& P, const EdgeClass<T>& C, const T* f,
+                                              const Strip<T, N>& S, int i, int j) {
+    using V2 = typename P2<T>::t;
+    const V2* const rows[3] = {S.xrow(j - 1), S.xrow(j), S.xrow(j + 1)};
+    V2 v[7];
+    T My, Ky, Ml, Kl, ay, al;
+    cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
+    const int64_t p = (int64_t)j * (N + 1) + i;
+    const T il = C.il[0];
+    S.rrow(j)[i] = pmake<T>((f[p] - ay) * il, (f[p + P.fs] - al) * (il * P.invd));
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void cl_ne_edge(const LevelP<T>& P, const EdgeClass<T>& C, const Strip<T, N>& S, int i,
+                                           int j) {
+    using V2 = typename P2<T>::t;
+    const V2* const rows[3] = {S.rrow(j - 1), S.rrow(j), S.rrow(j + 1)};
+    V2 v[7];
+    T My, Ky, Ml, Kl, qy, ql;
+    cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    const T il = C.il[0];
+    V2* xr = S.xrow(j);
+    V2 u = xr[i];
+    u.x += P.tau * il * qy;
+    u.y += P.tau * (il * P.invd) * ql;
+    xr[i] = u;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass<T>& C, int field,
+                                             const Strip<T, N>& S, int i, int j) {
+    using V2 = typename P2<T>::t;
+    V2* const rows[3] = {S.rrow(j - 1), S.rrow(j), S.rrow(j + 1)};
+    V2 v[7];
+    T My, Ky, Ml, Kl, qy, ql;
+    cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    const T p = field == 0 ? qy * C.iny : ql * C.inl;
+    V2* xr = S.xrow(j);
+    if (field == 0) xr[i].x += p;
+    else xr[i].y += p;
+    // column of A for this unknown: field y -> (m, cK); field lambda -> (cK, -dm)
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        const int ii = i + DI(o), jj = j + DJ(o);
+        if (!in_grid(ii, jj, N)) continue;
+        const T il = C.il[o];
+        const T mp = C.m[o] * p;
+        const T kp = P.c * (C.kd[o] * p + P.km * mp);
+        V2* q = rows[DJ(o) + 1] + ii;
+        if (field == 0) *q = pmake<T>(v[o].x - mp * il, v[o].y - kp * (il * P.invd));
+        else *q = pmake<T>(v[o].x - kp * il, v[o].y + mp * il);
+    }
+}
+
+// Edge nodes of a strip, enumerated per pass: the strip's full boundary rows
+// (rows 0, 1 in the first block, n-1, n in the last) slot by slot, then the
+// columns 0, 1, n-1, n of its other rows (four candidates per row).  c < 0:
+// every colour.
+template <int N>
+struct StripEdges {
+    static constexpr int FPR = (N + 1 + 6) / 7;  // slots of one colour per full row
+    int nfull, first_full_hi, ja, nrows;
+    __device__ __forceinline__ int count(int c) const { return nfull * (c < 0 ? N + 1 : FPR) + 4 * nrows; }
+    __device__ __forceinline__ bool node(int t, int c, int& i, int& j) const {
+        const int per = c < 0 ? N + 1 : FPR;
+        if (t < nfull * per) {
+            const int r = t / per, k = t - r * per;
+            j = r < first_full_hi ? r : N - 1 + (r - first_full_hi);
+            i = c < 0 ? k : ((c - 2 * j) % 7 + 7) % 7 + 7 * k;
+            return i <= N;
+        }
+        t -= nfull * per;
+        const int q = t & 3;
+        j = ja + (t >> 2);
+        i = q < 2 ? q : N - 3 + q;
+        return c < 0 || (i + 2 * j) % 7 == c;
+    }
+};
+
+// ------------------------------------------------------------- kernel --
+// Deep-interior nodes of the strip (rows and columns 2..N-2; warp-rounded
+// count) come first in every pass, then the strip's tabulated edge entries, so
+// that no warp mixes the two paths.
+template <typename T, int N>
+__global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T> P, int smoother, int steps,
+                                                                       T* __restrict__ x, const T* __restrict__ f) {
+    using V2 = typename P2<T>::t;
+    constexpr int LD = N + 1;
+    constexpr int W = N - 3;             // deep-interior columns
+    constexpr int CPR = (N - 3 + 6) / 7;  // slots per row of one colour
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int rmax = (N + 1 + cs - 1) / cs;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* X = reinterpret_cast<V2*>(smem_raw);
+    V2* R = X + rmax * LD;  // same offset in every block of the cluster
+    __shared__ EdgeClass<T> s_cls[25];
+
+    Strip<T, N> S;
+    S.r0 = cluster_row_lo(rank, N + 1, cs);
+    S.r1 = cluster_row_lo(rank + 1, N + 1, cs);
+    S.X = X;
+    S.R = R;
+    S.Xb = S.Rb = S.Xa = S.Ra = nullptr;
+    if (rank > 0) {
+        const int lb = S.r0 - 1 - cluster_row_lo(rank - 1, N + 1, cs);  // local index of row r0-1 below
+        S.Xb = cl.map_shared_rank(X, rank - 1) + lb * LD;
+        S.Rb = cl.map_shared_rank(R, rank - 1) + lb * LD;
+    }
+    if (rank < cs - 1) {
+        S.Xa = cl.map_shared_rank(X, rank + 1);
+        S.Ra = cl.map_shared_rank(R, rank + 1);
+    }
+
+    const int g = threadIdx.x, G = blockDim.x;
+    if (g < 25) edge_class_init<T, N>(P, g, s_cls[g]);
+    const int nown = (S.r1 - S.r0) * LD;
+    const int64_t base = (int64_t)S.r0 * LD;
+    for (int t = g; t < nown; t += G) X[t] = pmake<T>(x[base + t], x[base + t + P.fs]);
+    // every block has loaded its strip (and is running) before any remote access
+    cluster_barrier();
+
+    const int ja = max(S.r0, 2), jb = min(S.r1, N - 1);
+    const int nrows = jb > ja ? jb - ja : 0;
+    const int nia = nrows * W, niap = (nia + 31) & ~31;
+    StripEdges<N> SE;
+    SE.first_full_hi = rank == 0 ? 2 : 0;
+    SE.nfull = SE.first_full_hi + (rank == cs - 1 ? 2 : 0);
+    SE.ja = ja;
+    SE.nrows = nrows;
+    const int nea = SE.count(-1);
+
+    auto resid_all = [&]() {
+        for (int t = g; t < niap + nea; t += G) {
+            if (t < niap) {
+                if (t < nia) {
+                    const int r = t / W, i = 2 + t - r * W, j = ja + r;
+                    const int64_t p = (int64_t)j * LD + i;
+                    S.rrow(j)[i] = rows_resid_fast<T>(P, S.xrow(j), S.xrow(j + 1), S.xrow(j - 1), i, f[p], f[p + P.fs]);
+                }
+            } else {
+                int i, j;
+                if (SE.node(t - niap, -1, i, j)) cl_resid_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], f, S, i, j);
+            }
+        }
+        cluster_barrier();
+    };
+    auto phase = [&](int field, int c) {
+        const int ni = nrows * CPR, nip = (ni + 31) & ~31;
+        const int ne = SE.count(c);
+        for (int t = g; t < nip + ne; t += G) {
+            if (t < nip) {
+                if (t < ni) {
+                    const int r = t / CPR, k = t - r * CPR, j = ja + r;
+                    const int i = 2 + ((c - 2 * j - 2) % 7 + 7) % 7 + 7 * k;
+                    if (i <= N - 2) rows_lsgs_fast<T>(P, field, S.xrow(j), S.rrow(j), S.rrow(j + 1), S.rrow(j - 1), i);
+                }
+            } else {
+                int i, j;
+                if (SE.node(t - nip, c, i, j))
+                    cl_lsgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], field, S, i, j);
+            }
+        }
+        cluster_barrier();
+    };
+
+    if (smoother == 0) {
+        for (int m = 0; m < steps; ++m) {
+            resid_all();
+            for (int t = g; t < niap + nea; t += G) {
+                if (t < niap) {
+                    if (t < nia) {
+                        const int r = t / W, i = 2 + t - r * W, j = ja + r;
+                        rows_ne_fast<T>(P, S.xrow(j), S.rrow(j), S.rrow(j + 1), S.rrow(j - 1), i);
+                    }
+                } else {
+                    int i, j;
+                    if (SE.node(t - niap, -1, i, j)) cl_ne_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], S, i, j);
+                }
+            }
+            cluster_barrier();
+        }
+    } else {
+        resid_all();
+        for (int m = 0; m < steps; ++m) {
+            for (int field = 0; field < 2; ++field)
+                for (int c = 0; c < 7; ++c) phase(field, colour_seq(c));
+            if (smoother == 2)
+                for (int field = 1; field >= 0; --field)
+                    for (int c = 6; c >= 0; --c) phase(field, colour_seq(c));
+        }
+    }
+    // after the last barrier no block touches another's shared memory
+    for (int t = g; t < nown; t += G) {
+        const V2 v = X[t];
+        x[base + t] = v.x;
+        x[base + t + P.fs] = v.y;
+    }
+}
+
+template <typename T, int N>
+cudaLaunchConfig_t cluster_config(int cs, cudaStream_t s, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(small_threads<T>(), 1, 1);
+    cfg.dynamicSmemBytes = cluster_smem<T>(N, cs);
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+}  // namespace
+
+#define AAOMG_CLUSTER_N(CALL) CALL(64) CALL(128) CALL(256)
+
+template <typename T>
+size_t cluster_smem(int n, int cs) {
+    const size_t rmax = (size_t)(n + 1 + cs - 1) / cs;
+    return 2 * rmax * (n + 1) * sizeof(typename P2<T>::t);
+}
+
+template <typename T>
+cudaError_t cluster_prepare() {
+    cudaError_t e = cudaSuccess;
+#define P_(N)                                                                                           \
+    if (e == cudaSuccess)                                                                               \
+        e = cudaFuncSetAttribute(k_smooth_cluster<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 kClusterSmemMax);                                                      \
+    if (e == cudaSuccess)                                                                               \
+        e = cudaFuncSetAttribute(k_smooth_cluster<T, N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    AAOMG_CLUSTER_N(P_)
+#undef P_
+    return e;
+}
+
+template <typename T>
+int cluster_max_active(int n, int cs) {
+    if (!cluster_level(n) || cs < 2 || cs > kClusterMax || (n + 1) / cs < 2) return 0;
+    if (cluster_smem<T>(n, cs) > (size_t)kClusterSmemMax) return 0;
+    cudaLaunchAttribute at[1];
+    int num = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (n) {
+#define C_(N)                                                                              \
+    case N: {                                                                              \
+        cudaLaunchConfig_t cfg = cluster_config<T, N>(cs, 0, at);                          \
+        e = cudaOccupancyMaxActiveClusters(&num, (void*)k_smooth_cluster<T, N>, &cfg);     \
+        break;                                                                             \
+    }
+        AAOMG_CLUSTER_N(C_)
+#undef C_
+    default: break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // a refused size is an answer, not a sticky error
+        return 0;
+    }
+    return num;
+}
+
+template <typename T>
+cudaError_t launch_smooth_cluster(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, int cs,
+                                  cudaStream_t s) {
+    cudaLaunchAttribute at[1];
+    switch (P.n) {
+#define C_(N)                                                                                 \
+    case N: {                                                                                 \
+        cudaLaunchConfig_t cfg = cluster_config<T, N>(cs, s, at);                             \
+        return cudaLaunchKernelEx(&cfg, k_smooth_cluster<T, N>, P, smoother, steps, x, f); \
+    }
+        AAOMG_CLUSTER_N(C_)
+#undef C_
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+#define AAOMG_CLUSTER_INST(T)                                                                                    \
+    template size_t cluster_smem<T>(int, int);                                                                   \
+    template cudaError_t cluster_prepare<T>();                                                                   \
+    template int cluster_max_active<T>(int, int);                                                                \
+    template cudaError_t launch_smooth_cluster<T>(const LevelP<T>&, int, int, T*, const T*, int, cudaStream_t);
+AAOMG_CLUSTER_INST(float)
+AAOMG_CLUSTER_INST(double)
+
+}  // namespace aaomg

@@ -25,23 +25,6 @@ namespace {
 
 
 // ----------------------------------------------- tabulated edge updates --
-template <typename T>
-struct EdgeRow {
-    int p, mask;
-    T m[7], kd[7];
-};
-
-template <typename T>
-__device__ __forceinline__ void edge_load(const EdgeTable<T>& E, int e, EdgeRow<T>& r) {
-    r.p = E.node[e];
-    r.mask = E.mask[e];
-#pragma unroll
-    for (int o = 0; o < 7; ++o) {
-        r.m[o] = E.m[o * E.total + e];
-        r.kd[o] = E.kd[o * E.total + e];
-    }
-}
-
 __device__ __forceinline__ int edge_off(int o, int ld) {
     return DI(o) + DJ(o) * ld;
 }

@@ -30,6 +30,17 @@ def test_binding_covers_header(lib):
         assert getattr(lib.load(), n).argtypes is not None, n
 
 
+def test_options_layout_matches_header(lib):
+    """The ctypes mirror of mg_options lists the header's fields in order with
+    the same C types."""
+    text = open(lib.HEADER).read()
+    body = re.search(r"typedef struct mg_options \{(.*?)\} mg_options;", text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(int|double)\s+(\w+)\s*;", body)
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double}
+    assert [(n, ctype[t]) for t, n in fields] == [(n, t) for n, t in lib.Options._fields_]
+
+
 def test_error_strings_without_device(lib):
     so = lib.load()
     assert so.mg_strerror(0) == b"ok"

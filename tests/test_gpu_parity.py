@@ -67,8 +67,9 @@ def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
 @pytest.mark.parametrize("L,small_max", [(6, 0), (8, 0), (10, 0), (6, -1), (8, -1), (9, 300)])
 def test_smoothing_call_kernels(mg, oracle_mod, L, small_max, smoother, precision):
     """The one-launch smoothing call (one block with the residual in shared
-    memory, or one cluster over L2-resident data) and the per-phase launches
-    (small_max = -1) give the oracle's steps."""
+    memory, or one cluster with x and the residual in its blocks' shared
+    memory) and the per-phase launches (small_max = -1) give the oracle's
+    steps."""
     alpha = 1e-2
     x0 = inputs.f32_exact(inputs.x_uniform(L, 500 + L))
     f = inputs.f32_exact(inputs.x_uniform(L, 600 + L))
@@ -79,6 +80,34 @@ def test_smoothing_call_kernels(mg, oracle_mod, L, small_max, smoother, precisio
             s.smooth(dev(f), x, steps)
             d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
             assert d <= TOL[precision], (steps, d)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("L,cs", [(6, 2), (6, 3), (6, 16), (7, 5), (7, 16), (8, 12), (8, 16)])
+def test_cluster_smoothing_call(mg, oracle_mod, L, cs, smoother, precision):
+    """The one-launch smoothing call on a cluster of cs blocks (grid rows split
+    into cs strips, uneven ones included; neighbouring strips reached through
+    distributed shared memory) gives the oracle's steps."""
+    alpha = 1e-2
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 700 + L))
+    f = inputs.f32_exact(inputs.x_uniform(L, 800 + L))
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother)
+    with mg.Solver(L, alpha, smoother=smoother, precision=precision, cluster_size=cs) as s:
+        for steps in (1, 2):
+            x = dev(x0)
+            s.smooth(dev(f), x, steps)
+            d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
+            assert d <= TOL[precision], (steps, d)
+
+
+@pytest.mark.parametrize("L,cs", [(8, 2), (7, 17), (6, 64)])
+def test_cluster_size_that_cannot_run(mg, L, cs):
+    """A forced cluster size whose strips do not fit in shared memory, or that
+    exceeds the cluster limit, is refused at set-up."""
+    with pytest.raises(mg.MGError) as e:
+        mg.Solver(L, 1e-2, smoother="lsgs", precision="fp32_refine", cluster_size=cs)
+    assert e.value.code == -1
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
