@@ -13,11 +13,10 @@
 
 #include "aaomg.h"
 #include "band.h"
-#include "cluster.h"
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
-#include "small.h"
+#include "strips.h"
 
 using namespace aaomg;
 
@@ -44,26 +43,13 @@ struct Lev {
     void* f = nullptr;
     void* rh = nullptr;
     BandGrid bg{};
-    bool block = false;      // smoothing calls in one launch of one block
-    int cs = 0;              // > 0: smoothing calls in one launch of a cluster of cs blocks
-    EdgeTable<float> ef{};   // tabulated edge nodes for the one-launch smoothing kernels
-    EdgeTable<double> ed{};
+    int cs = 0;              // smoothing calls in one launch: of one block (1) or a cluster of cs blocks; 0: no
     LevelP<float> pf{};
     LevelP<double> pd{};
 };
 
 template <typename T>
 const LevelP<T>& lp(const Lev& v);
-template <typename T>
-const EdgeTable<T>& etab(const Lev& v);
-template <>
-const EdgeTable<float>& etab<float>(const Lev& v) {
-    return v.ef;
-}
-template <>
-const EdgeTable<double>& etab<double>(const Lev& v) {
-    return v.ed;
-}
 template <typename T>
 const CtaParams<T>& ctap(const mg_ctx* H);
 template <>
@@ -302,15 +288,9 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* f = (T*)v.f;
     T* rh = (T*)v.rh;
     if (v.cs > 0) {
-        // the whole smoothing call in one launch of one cluster (x and rh in
-        // the blocks' shared memory)
-        launch_smooth_cluster<T>(P, H->o.smoother, steps, x, f, v.cs, s);
-        H->rec_kernels += 1;
-        return;
-    }
-    if (v.block) {
-        // the whole smoothing call in one launch of one block (rh in shared memory)
-        launch_smooth_block<T>(P, etab<T>(v), H->o.smoother, steps, x, f, s);
+        // the whole smoothing call in one launch of one block or one cluster
+        // (x and rh in shared memory)
+        launch_smooth_strips<T>(P, H->o.smoother, steps, x, f, v.cs, s);
         H->rec_kernels += 1;
         return;
     }
@@ -422,74 +402,13 @@ int record_iteration(mg_ctx* H, cudaStream_t s) {
     return AAOMG_OK;
 }
 
-// Tabulated edge nodes of level v (see edge.h), in the cycle's precision.
-// blocks per cluster of the one-launch smoothing call by level size and
-// precision (measured on GB300): 0 keeps the single-block kernel, which wins on
-// 65 x 65 nodes in FP32
+// blocks of the one-launch smoothing call by level size and precision,
+// measured on GB300 (1: a single block)
 int default_cluster(int n, bool fp32) {
-    if (n <= 64) return fp32 ? 0 : 8;
+    if (n <= 32) return 1;
+    if (n <= 64) return fp32 ? 1 : 8;
     if (n <= 128) return fp32 ? 8 : 16;
     return 16;
-}
-
-template <typename T>
-int build_edge_table(mg_ctx* H, Lev& v, double km, EdgeTable<T>& E) {
-    const int n = v.n;
-    const Coef K = make_coef(n, H->alpha, H->fp32, km);
-    std::vector<int> nodes[7];
-    for (int j = 0; j <= n; ++j)
-        for (int i = 0; i <= n; ++i)
-            if (i < 2 || i > n - 2 || j < 2 || j > n - 2) nodes[(i + 2 * j) % 7].push_back(j * (n + 1) + i);
-    int total = 0;
-    for (int c = 0; c < 7; ++c) {
-        E.start[c] = total;
-        E.count[c] = (int)nodes[c].size();
-        total += E.count[c];
-    }
-    E.total = total;
-    std::vector<T> m(7 * (size_t)total), kd(7 * (size_t)total), il(7 * (size_t)total), iny(total), inl(total);
-    std::vector<int> node(total), mask(total);
-    int e = 0;
-    for (int c = 0; c < 7; ++c)
-        for (int p : nodes[c]) {
-            int i = p % (n + 1), j = p / (n + 1);
-            double mm[7], kk[7];
-            row_coeffs_general<double>(i, j, n, K.h2, mm, kk);
-            int mk = 0;
-            for (int o = 0; o < 7; ++o) {
-                int ii = i + DI(o), jj = j + DJ(o);
-                bool in = in_grid(ii, jj, n);
-                if (in) mk |= 1 << o;
-                m[(size_t)o * total + e] = (T)mm[o];
-                kd[(size_t)o * total + e] = (T)kk[o];
-                il[(size_t)o * total + e] = in ? (T)(1.0 / coef_ly(K, ii, jj)) : T(0);
-            }
-            node[e] = p;
-            mask[e] = mk;
-            iny[e] = (T)(1.0 / coef_nd(K, i, j, 0));
-            inl[e] = (T)(1.0 / coef_nd(K, i, j, 1));
-            ++e;
-        }
-    size_t tb = sizeof(T) * (size_t)total, ib = sizeof(int) * (size_t)total;
-    void* buf = nullptr;
-    int rc = dalloc(H, &buf, 23 * tb + 2 * ib);
-    if (rc) return rc;
-    char* b = (char*)buf;
-    E.m = (T*)b;
-    E.kd = (T*)(b + 7 * tb);
-    E.il = (T*)(b + 14 * tb);
-    E.inv_ny = (T*)(b + 21 * tb);
-    E.inv_nl = (T*)(b + 22 * tb);
-    E.node = (int*)(b + 23 * tb);
-    E.mask = (int*)(b + 23 * tb + ib);
-    CK(cudaMemcpy(E.m, m.data(), 7 * tb, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(E.kd, kd.data(), 7 * tb, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(E.il, il.data(), 7 * tb, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(E.inv_ny, iny.data(), tb, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(E.inv_nl, inl.data(), tb, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(E.node, node.data(), ib, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(E.mask, mask.data(), ib, cudaMemcpyHostToDevice));
-    return AAOMG_OK;
 }
 
 // Dense map of the gamma coarse-grid steps on level ld (from a zero initial
@@ -732,8 +651,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         H->band_min = H->small_max + 1 > 2049 ? H->small_max + 1 : 2049;
     }
     {
-        cudaError_t e = H->fp32 ? small_prepare<float>() : small_prepare<double>();
-        if (e == cudaSuccess) e = H->fp32 ? cluster_prepare<float>() : cluster_prepare<double>();
+        cudaError_t e = H->fp32 ? strips_prepare<float>() : strips_prepare<double>();
         if (e != cudaSuccess) {
             delete H;
             return fail(AAOMG_ERR_CUDA, std::string("smoothing kernel attributes: ") + cudaGetErrorString(e));
@@ -775,30 +693,28 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         return rc;
     }
     // One-launch smoothing calls on the levels with at most small_max nodes per
-    // side: a cluster of blocks on the mid-size levels (with the cluster size
-    // cluster_size, else one by level size), a single block on the small ones.
+    // side: a cluster of cluster_size blocks on the mid-size levels if asked,
+    // else the measured choice by level size and precision; a single block
+    // where that is chosen or no cluster can run.
     for (int l = 2; l <= levels && !rc; ++l) {
         Lev& v = H->lev[l];
         if (v.n + 1 > H->small_max) continue;
-        if (cluster_level(v.n) && o.cluster_size != 1) {
-            auto runs = [&](int cs) {
-                return (H->fp32 ? cluster_max_active<float>(v.n, cs) : cluster_max_active<double>(v.n, cs)) > 0;
-            };
-            if (o.cluster_size > 1) {
-                if (runs(o.cluster_size)) v.cs = o.cluster_size;
-                else
-                    rc = fail(AAOMG_ERR_BAD_ARG, "cluster_size " + std::to_string(o.cluster_size) +
-                                                     " cannot run on a level with " + std::to_string(v.n + 1) +
-                                                     " nodes per side");
-            } else {
-                for (int cs = default_cluster(v.n, H->fp32); cs >= 2 && !v.cs; cs /= 2)
-                    if (runs(cs)) v.cs = cs;
-            }
+        auto runs = [&](int cs) {
+            return (H->fp32 ? strips_max_active<float>(v.n, cs) : strips_max_active<double>(v.n, cs)) > 0;
+        };
+        if (o.cluster_size > 1 && cluster_level(v.n)) {
+            if (runs(o.cluster_size)) v.cs = o.cluster_size;
+            else
+                rc = fail(AAOMG_ERR_BAD_ARG, "cluster_size " + std::to_string(o.cluster_size) +
+                                                 " cannot run on a level with " + std::to_string(v.n + 1) +
+                                                 " nodes per side");
+        } else if (o.cluster_size == 1) {
+            v.cs = runs(1) ? 1 : 0;
+        } else {
+            for (int cs = default_cluster(v.n, H->fp32); cs >= 2 && !v.cs; cs /= 2)
+                if (runs(cs)) v.cs = cs;
+            if (!v.cs && runs(1)) v.cs = 1;
         }
-        v.block = !v.cs && v.n <= 128 &&
-                  (H->fp32 ? block_smooth_smem<float>(v.n) : block_smooth_smem<double>(v.n)) <= (size_t)kBlockSmemMax;
-        if (!rc && v.block)
-            rc = H->fp32 ? build_edge_table<float>(H, v, km, v.ef) : build_edge_table<double>(H, v, km, v.ed);
     }
     if (rc) {
         mg_destroy(H);

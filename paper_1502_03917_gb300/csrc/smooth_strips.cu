@@ -1,29 +1,29 @@
-// smooth_cluster.cu -- a whole smoothing call (nu steps of Algorithm 1 or 2) on
-// one mid-size level (65 to 257 nodes per side) in ONE launch of ONE
-// thread-block cluster.
+// smooth_strips.cu -- a whole smoothing call (nu steps of Algorithm 1 or 2) on
+// one small or mid-size level in ONE launch: of one thread block (levels up to
+// 65 x 65 nodes) or of one thread-block cluster (65 to 257 nodes per side).
 //
-// On these levels a colour phase of Algorithm 2 has a few hundred to a few
-// thousand independent updates: too few to fill the GPU, too many for one
-// block to finish quickly, and a launch per phase costs more than the phase.
-// Here the level's grid rows are split into cs strips, one per block of a
-// cluster (cs = 4 to 16 SMs).  Each block keeps the iterate x and the scaled
-// residual rh = L^{-1}(f - Ax) of its strip in its own shared memory as
-// (y, lambda) pairs for the whole call; x is read from global memory once at
-// the start and written back once at the end.  A node in the first or last row
+// On these levels a colour phase of Algorithm 2 has a few dozen to a few
+// thousand independent updates: too few to fill the GPU, and a launch per phase
+// costs more than the phase.  The kernel loops over the phases with a barrier
+// between dependent ones instead.  The level's grid rows are split into cs
+// strips, one per block (cs = 1 for a single block, up to 16 blocks of a
+// cluster).  Each block keeps the iterate x and the scaled residual
+// rh = L^{-1}(f - Ax) of its strip in its own shared memory as (y, lambda)
+// pairs for the whole call; x is read from global memory once at the start and
+// written back once at the end.  In a cluster, a node in the first or last row
 // of a strip reaches one row into the neighbouring strip: those loads and, for
 // Algorithm 2, the residual updates of the scatter go to the neighbouring
-// block's shared memory (distributed shared memory).  The phases are separated
-// by cluster barriers (release / acquire), which also make those remote stores
-// visible.  Within a colour phase no two updates touch a common unknown or
-// residual entry (distance-2 colouring), so the result is the sequential
-// multicolour sweep's whatever the strips.
+// block's shared memory (distributed shared memory), and the phases are
+// separated by cluster barriers (release / acquire), which also make those
+// remote stores visible.  Within a colour phase no two updates touch a common
+// unknown or residual entry (distance-2 colouring), so the result is the
+// sequential multicolour sweep's whatever the strips.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
-#include "cluster.h"
 #include "lean.cuh"
-#include "small.h"
 #include "stencil.cuh"
+#include "strips.h"
 
 namespace cg = cooperative_groups;
 
@@ -38,9 +38,11 @@ __device__ __forceinline__ void cluster_barrier() {
             : "memory");
 }
 
-// The strip of this block: own rows [r0, r1) in shared memory, and the
-// boundary rows of the neighbouring strips (null at the grid's bottom / top).
-template <typename T, int N>
+// The strip of this block: own rows [r0, r1) in shared memory, and in a
+// cluster the boundary rows of the neighbouring strips (null at the grid's
+// bottom / top).  A single block (CL = false) owns every row, so all row
+// pointers point into its own shared memory.
+template <typename T, int N, bool CL>
 struct Strip {
     using V2 = typename P2<T>::t;
     static constexpr int LD = N + 1;
@@ -49,15 +51,23 @@ struct Strip {
     V2 *Xb, *Rb;  // row r0 - 1 (last row of the block below)
     V2 *Xa, *Ra;  // row r1 (first row of the block above)
     // rows j in [r0 - 1, r1]
-    __device__ __forceinline__ V2* xrow(int j) const { return j < r0 ? Xb : (j >= r1 ? Xa : X + (j - r0) * LD); }
-    __device__ __forceinline__ V2* rrow(int j) const { return j < r0 ? Rb : (j >= r1 ? Ra : R + (j - r0) * LD); }
+    __device__ __forceinline__ V2* xrow(int j) const {
+        if constexpr (!CL) return X + j * LD;
+        else return j < r0 ? Xb : (j >= r1 ? Xa : X + (j - r0) * LD);
+    }
+    __device__ __forceinline__ V2* rrow(int j) const {
+        if constexpr (!CL) return R + j * LD;
+        else return j < r0 ? Rb : (j >= r1 ? Ra : R + (j - r0) * LD);
+    }
 };
 
 // ------------------------------------------------------- edge nodes --
 // Nodes within two rows or columns of the boundary.  Their stencils, the L_y^-1
 // of their neighbours and their N_ii^-1 depend only on the node's boundary
 // class cls5(i) + 5 cls5(j); each block tabulates the 25 classes in shared
-// memory at the start (no global-memory latency inside a phase).
+// memory at the start (no global-memory latency inside a phase).  An LSGS
+// update reads the table entries its scatter needs before its first store, so
+// that no table load waits behind a store it might alias.
 template <typename T>
 struct EdgeClass {
     T m[7], kd[7], il[7];  // il: L_y^-1 of neighbour o (0 outside the grid)
@@ -94,9 +104,9 @@ __device__ __forceinline__ void cl_gather(const RowPtr (&rows)[3], int i, int j,
     }
 }
 
-template <typename T, int N>
-__device__ __forceinline__ void cl_resid_edge(const LevelP<T>& P, const EdgeClass<T>& C, const T* f,
-                                              const Strip<T, N>& S, int i, int j) {
+template <typename T, int N, class S_>
+__device__ __forceinline__ void cl_resid_edge(const LevelP<T>& P, const EdgeClass<T>& C, const T* f, const S_& S,
+                                              int i, int j) {
     using V2 = typename P2<T>::t;
     const V2* const rows[3] = {S.xrow(j - 1), S.xrow(j), S.xrow(j + 1)};
     V2 v[7];
@@ -108,9 +118,8 @@ __device__ __forceinline__ void cl_resid_edge(const LevelP<T>& P, const EdgeClas
     S.rrow(j)[i] = pmake<T>((f[p] - ay) * il, (f[p + P.fs] - al) * (il * P.invd));
 }
 
-template <typename T, int N>
-__device__ __forceinline__ void cl_ne_edge(const LevelP<T>& P, const EdgeClass<T>& C, const Strip<T, N>& S, int i,
-                                           int j) {
+template <typename T, int N, class S_>
+__device__ __forceinline__ void cl_ne_edge(const LevelP<T>& P, const EdgeClass<T>& C, const S_& S, int i, int j) {
     using V2 = typename P2<T>::t;
     const V2* const rows[3] = {S.rrow(j - 1), S.rrow(j), S.rrow(j + 1)};
     V2 v[7];
@@ -125,16 +134,20 @@ __device__ __forceinline__ void cl_ne_edge(const LevelP<T>& P, const EdgeClass<T
     xr[i] = u;
 }
 
-template <typename T, int N>
-__device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass<T>& C, int field,
-                                             const Strip<T, N>& S, int i, int j) {
+template <typename T, int N, class S_>
+__device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass<T>& C, int field, const S_& S,
+                                             int i, int j) {
     using V2 = typename P2<T>::t;
+    T il[7];  // read before the first store
+#pragma unroll
+    for (int o = 0; o < 7; ++o) il[o] = C.il[o];
+    const T inv_nd = field == 0 ? C.iny : C.inl;
     V2* const rows[3] = {S.rrow(j - 1), S.rrow(j), S.rrow(j + 1)};
     V2 v[7];
     T My, Ky, Ml, Kl, qy, ql;
     cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
     rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
-    const T p = field == 0 ? qy * C.iny : ql * C.inl;
+    const T p = (field == 0 ? qy : ql) * inv_nd;
     V2* xr = S.xrow(j);
     if (field == 0) xr[i].x += p;
     else xr[i].y += p;
@@ -143,24 +156,25 @@ __device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass
     for (int o = 0; o < 7; ++o) {
         const int ii = i + DI(o), jj = j + DJ(o);
         if (!in_grid(ii, jj, N)) continue;
-        const T il = C.il[o];
         const T mp = C.m[o] * p;
         const T kp = P.c * (C.kd[o] * p + P.km * mp);
         V2* q = rows[DJ(o) + 1] + ii;
-        if (field == 0) *q = pmake<T>(v[o].x - mp * il, v[o].y - kp * (il * P.invd));
-        else *q = pmake<T>(v[o].x - kp * il, v[o].y + mp * il);
+        if (field == 0) *q = pmake<T>(v[o].x - mp * il[o], v[o].y - kp * (il[o] * P.invd));
+        else *q = pmake<T>(v[o].x - kp * il[o], v[o].y + mp * il[o]);
     }
 }
 
 // Edge nodes of a strip, enumerated per pass: the strip's full boundary rows
 // (rows 0, 1 in the first block, n-1, n in the last) slot by slot, then the
-// columns 0, 1, n-1, n of its other rows (four candidates per row).  c < 0:
-// every colour.
+// columns 0, 1, n-1, n of its other rows.  For one colour c the nodes of column
+// i sit in the rows j = 4 (c - i) mod 7 (2 j = c - i mod 7), every 7th row, so
+// each column gets ceil(rows / 7) slots; c < 0 (every colour): every row.
 template <int N>
 struct StripEdges {
     static constexpr int FPR = (N + 1 + 6) / 7;  // slots of one colour per full row
     int nfull, first_full_hi, ja, nrows;
-    __device__ __forceinline__ int count(int c) const { return nfull * (c < 0 ? N + 1 : FPR) + 4 * nrows; }
+    __device__ __forceinline__ int per_col(int c) const { return c < 0 ? nrows : (nrows + 6) / 7; }
+    __device__ __forceinline__ int count(int c) const { return nfull * (c < 0 ? N + 1 : FPR) + 4 * per_col(c); }
     __device__ __forceinline__ bool node(int t, int c, int& i, int& j) const {
         const int per = c < 0 ? N + 1 : FPR;
         if (t < nfull * per) {
@@ -170,57 +184,72 @@ struct StripEdges {
             return i <= N;
         }
         t -= nfull * per;
-        const int q = t & 3;
-        j = ja + (t >> 2);
+        const int pc = per_col(c);
+        int q = 0, k = t;
+        while (k >= pc && q < 3) {  // q = t / pc for t < 4 pc
+            k -= pc;
+            ++q;
+        }
         i = q < 2 ? q : N - 3 + q;
-        return c < 0 || (i + 2 * j) % 7 == c;
+        j = c < 0 ? ja + k : ja + ((4 * (c - i) - ja) % 7 + 7) % 7 + 7 * k;
+        return j < ja + nrows;
     }
 };
 
 // ------------------------------------------------------------- kernel --
 // Deep-interior nodes of the strip (rows and columns 2..N-2; warp-rounded
-// count) come first in every pass, then the strip's tabulated edge entries, so
-// that no warp mixes the two paths.
-template <typename T, int N>
-__global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T> P, int smoother, int steps,
-                                                                       T* __restrict__ x, const T* __restrict__ f) {
+// count) come first in every pass, then the strip's edge nodes, so that no warp
+// mixes the two paths.
+template <typename T, int N, bool CL>
+__global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> P, int smoother, int steps,
+                                                                      T* __restrict__ x, const T* __restrict__ f) {
     using V2 = typename P2<T>::t;
     constexpr int LD = N + 1;
     constexpr int W = N - 3;             // deep-interior columns
     constexpr int CPR = (N - 3 + 6) / 7;  // slots per row of one colour
-    cg::cluster_group cl = cg::this_cluster();
-    const int cs = (int)cl.num_blocks();
-    const int rank = (int)cl.block_rank();
+    int cs = 1, rank = 0;
+    if constexpr (CL) {
+        cs = (int)cg::this_cluster().num_blocks();
+        rank = (int)cg::this_cluster().block_rank();
+    }
     const int rmax = (N + 1 + cs - 1) / cs;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2* X = reinterpret_cast<V2*>(smem_raw);
-    V2* R = X + rmax * LD;  // same offset in every block of the cluster
+    V2* R = X + rmax * LD;  // same offset in every block of a cluster
     __shared__ EdgeClass<T> s_cls[25];
 
-    Strip<T, N> S;
-    S.r0 = cluster_row_lo(rank, N + 1, cs);
-    S.r1 = cluster_row_lo(rank + 1, N + 1, cs);
+    Strip<T, N, CL> S;
+    S.r0 = strip_row_lo(rank, N + 1, cs);
+    S.r1 = strip_row_lo(rank + 1, N + 1, cs);
     S.X = X;
     S.R = R;
     S.Xb = S.Rb = S.Xa = S.Ra = nullptr;
-    if (rank > 0) {
-        const int lb = S.r0 - 1 - cluster_row_lo(rank - 1, N + 1, cs);  // local index of row r0-1 below
-        S.Xb = cl.map_shared_rank(X, rank - 1) + lb * LD;
-        S.Rb = cl.map_shared_rank(R, rank - 1) + lb * LD;
+    if constexpr (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (rank > 0) {
+            const int lb = S.r0 - 1 - strip_row_lo(rank - 1, N + 1, cs);  // local index of row r0-1 below
+            S.Xb = cl.map_shared_rank(X, rank - 1) + lb * LD;
+            S.Rb = cl.map_shared_rank(R, rank - 1) + lb * LD;
+        }
+        if (rank < cs - 1) {
+            S.Xa = cl.map_shared_rank(X, rank + 1);
+            S.Ra = cl.map_shared_rank(R, rank + 1);
+        }
     }
-    if (rank < cs - 1) {
-        S.Xa = cl.map_shared_rank(X, rank + 1);
-        S.Ra = cl.map_shared_rank(R, rank + 1);
-    }
+    // between dependent phases; in a cluster, also before the first remote
+    // access (every block has loaded its strip and is running)
+    auto barrier = [&]() {
+        if constexpr (CL) cluster_barrier();
+        else __syncthreads();
+    };
 
     const int g = threadIdx.x, G = blockDim.x;
     if (g < 25) edge_class_init<T, N>(P, g, s_cls[g]);
     const int nown = (S.r1 - S.r0) * LD;
     const int64_t base = (int64_t)S.r0 * LD;
     for (int t = g; t < nown; t += G) X[t] = pmake<T>(x[base + t], x[base + t + P.fs]);
-    // every block has loaded its strip (and is running) before any remote access
-    cluster_barrier();
+    barrier();
 
     const int ja = max(S.r0, 2), jb = min(S.r1, N - 1);
     const int nrows = jb > ja ? jb - ja : 0;
@@ -245,7 +274,7 @@ __global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T>
                 if (SE.node(t - niap, -1, i, j)) cl_resid_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], f, S, i, j);
             }
         }
-        cluster_barrier();
+        barrier();
     };
     auto phase = [&](int field, int c) {
         const int ni = nrows * CPR, nip = (ni + 31) & ~31;
@@ -263,7 +292,7 @@ __global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T>
                     cl_lsgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], field, S, i, j);
             }
         }
-        cluster_barrier();
+        barrier();
     };
 
     if (smoother == 0) {
@@ -280,7 +309,7 @@ __global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T>
                     if (SE.node(t - niap, -1, i, j)) cl_ne_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], S, i, j);
                 }
             }
-            cluster_barrier();
+            barrier();
         }
     } else {
         resid_all();
@@ -300,59 +329,77 @@ __global__ void __launch_bounds__(small_threads<T>()) k_smooth_cluster(LevelP<T>
     }
 }
 
-template <typename T, int N>
-cudaLaunchConfig_t cluster_config(int cs, cudaStream_t s, cudaLaunchAttribute* at) {
+template <typename T, int N, bool CL>
+cudaLaunchConfig_t strips_config(int cs, cudaStream_t s, cudaLaunchAttribute* at) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
-    cfg.blockDim = dim3(small_threads<T>(), 1, 1);
-    cfg.dynamicSmemBytes = cluster_smem<T>(N, cs);
+    cfg.blockDim = dim3(strip_threads<T>(), 1, 1);
+    cfg.dynamicSmemBytes = strips_smem<T>(N, cs);
     cfg.stream = s;
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 0;
+    if (CL) {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.numAttrs = 1;
+    }
     return cfg;
 }
 
 }  // namespace
 
+// instantiated level sizes: single block for n = 4 .. 64, cluster for 64 .. 256
+#define AAOMG_BLOCK_N(CALL) CALL(4) CALL(8) CALL(16) CALL(32) CALL(64)
 #define AAOMG_CLUSTER_N(CALL) CALL(64) CALL(128) CALL(256)
 
 template <typename T>
-size_t cluster_smem(int n, int cs) {
+size_t strips_smem(int n, int cs) {
     const size_t rmax = (size_t)(n + 1 + cs - 1) / cs;
     return 2 * rmax * (n + 1) * sizeof(typename P2<T>::t);
 }
 
 template <typename T>
-cudaError_t cluster_prepare() {
+cudaError_t strips_prepare() {
     cudaError_t e = cudaSuccess;
-#define P_(N)                                                                                           \
+#define B_(N)                                                                                            \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_smooth_strips<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 kStripSmemMax);
+#define C_(N)                                                                                           \
     if (e == cudaSuccess)                                                                               \
-        e = cudaFuncSetAttribute(k_smooth_cluster<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 kClusterSmemMax);                                                      \
+        e = cudaFuncSetAttribute(k_smooth_strips<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 kStripSmemMax);                                                        \
     if (e == cudaSuccess)                                                                               \
-        e = cudaFuncSetAttribute(k_smooth_cluster<T, N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    AAOMG_CLUSTER_N(P_)
-#undef P_
+        e = cudaFuncSetAttribute(k_smooth_strips<T, N, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    AAOMG_BLOCK_N(B_)
+    AAOMG_CLUSTER_N(C_)
+#undef B_
+#undef C_
     return e;
 }
 
 template <typename T>
-int cluster_max_active(int n, int cs) {
-    if (!cluster_level(n) || cs < 2 || cs > kClusterMax || (n + 1) / cs < 2) return 0;
-    if (cluster_smem<T>(n, cs) > (size_t)kClusterSmemMax) return 0;
+bool strips_fit(int n, int cs) {
+    if (cs < 1 || cs > kClusterMax || (cs > 1 && (n + 1) / cs < 2)) return false;
+    if (cs == 1 ? !block_level(n) : !cluster_level(n)) return false;
+    return strips_smem<T>(n, cs) <= (size_t)kStripSmemMax;
+}
+
+template <typename T>
+int strips_max_active(int n, int cs) {
+    if (!strips_fit<T>(n, cs)) return 0;
+    if (cs == 1) return 1;
     cudaLaunchAttribute at[1];
     int num = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (n) {
-#define C_(N)                                                                              \
-    case N: {                                                                              \
-        cudaLaunchConfig_t cfg = cluster_config<T, N>(cs, 0, at);                          \
-        e = cudaOccupancyMaxActiveClusters(&num, (void*)k_smooth_cluster<T, N>, &cfg);     \
-        break;                                                                             \
+#define C_(N)                                                                                  \
+    case N: {                                                                                  \
+        cudaLaunchConfig_t cfg = strips_config<T, N, true>(cs, 0, at);                         \
+        e = cudaOccupancyMaxActiveClusters(&num, (void*)k_smooth_strips<T, N, true>, &cfg);    \
+        break;                                                                                 \
     }
         AAOMG_CLUSTER_N(C_)
 #undef C_
@@ -366,14 +413,26 @@ int cluster_max_active(int n, int cs) {
 }
 
 template <typename T>
-cudaError_t launch_smooth_cluster(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, int cs,
-                                  cudaStream_t s) {
+cudaError_t launch_smooth_strips(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, int cs,
+                                 cudaStream_t s) {
     cudaLaunchAttribute at[1];
+    if (cs == 1) {
+        switch (P.n) {
+#define B_(N)                                                                                        \
+    case N: {                                                                                        \
+        cudaLaunchConfig_t cfg = strips_config<T, N, false>(1, s, at);                               \
+        return cudaLaunchKernelEx(&cfg, k_smooth_strips<T, N, false>, P, smoother, steps, x, f);     \
+    }
+            AAOMG_BLOCK_N(B_)
+#undef B_
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (P.n) {
-#define C_(N)                                                                                 \
-    case N: {                                                                                 \
-        cudaLaunchConfig_t cfg = cluster_config<T, N>(cs, s, at);                             \
-        return cudaLaunchKernelEx(&cfg, k_smooth_cluster<T, N>, P, smoother, steps, x, f); \
+#define C_(N)                                                                                       \
+    case N: {                                                                                       \
+        cudaLaunchConfig_t cfg = strips_config<T, N, true>(cs, s, at);                              \
+        return cudaLaunchKernelEx(&cfg, k_smooth_strips<T, N, true>, P, smoother, steps, x, f);     \
     }
         AAOMG_CLUSTER_N(C_)
 #undef C_
@@ -381,12 +440,13 @@ cudaError_t launch_smooth_cluster(const LevelP<T>& P, int smoother, int steps, T
     }
 }
 
-#define AAOMG_CLUSTER_INST(T)                                                                                    \
-    template size_t cluster_smem<T>(int, int);                                                                   \
-    template cudaError_t cluster_prepare<T>();                                                                   \
-    template int cluster_max_active<T>(int, int);                                                                \
-    template cudaError_t launch_smooth_cluster<T>(const LevelP<T>&, int, int, T*, const T*, int, cudaStream_t);
-AAOMG_CLUSTER_INST(float)
-AAOMG_CLUSTER_INST(double)
+#define AAOMG_STRIPS_INST(T)                                                                                    \
+    template size_t strips_smem<T>(int, int);                                                                   \
+    template cudaError_t strips_prepare<T>();                                                                   \
+    template bool strips_fit<T>(int, int);                                                                      \
+    template int strips_max_active<T>(int, int);                                                                \
+    template cudaError_t launch_smooth_strips<T>(const LevelP<T>&, int, int, T*, const T*, int, cudaStream_t);
+AAOMG_STRIPS_INST(float)
+AAOMG_STRIPS_INST(double)
 
 }  // namespace aaomg

@@ -1,0 +1,46 @@
+// strips.h -- one-launch smoothing calls on small and mid-size levels
+// (internal): one thread block, or one thread-block cluster whose blocks each
+// own a strip of grid rows.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace aaomg {
+
+// threads per block (FP64 needs more registers per thread)
+template <typename T>
+constexpr int strip_threads() {
+    return sizeof(T) == 4 ? 1024 : 512;
+}
+// dynamic shared memory per block: 227 KB less room for a small static table
+constexpr int kStripSmemMax = 227 * 1024 - 8 * 1024;
+constexpr int kClusterMax = 16;  // blocks per cluster; above 8 needs the non-portable size
+
+// level sizes (cells per side) with a single-block kernel and with a cluster kernel
+constexpr bool block_level(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
+constexpr bool cluster_level(int n) { return n == 64 || n == 128 || n == 256; }
+
+// rows [row_lo(k), row_lo(k+1)) of a level with `rows` grid rows belong to
+// block k of cs blocks
+AAOMG_HD int strip_row_lo(int k, int rows, int cs) { return (int)(((long long)k * rows) / cs); }
+
+// shared memory per block: x and rh pairs of the largest strip
+template <typename T>
+size_t strips_smem(int n, int cs);
+template <typename T>
+cudaError_t strips_prepare();
+// whether cs blocks (1: a single block) have a kernel for n and fit in shared memory
+template <typename T>
+bool strips_fit(int n, int cs);
+// clusters of cs blocks that can be resident at once on this device (0: the
+// configuration cannot run; 1 for a fitting single block)
+template <typename T>
+int strips_max_active(int n, int cs);
+// `steps` smoothing steps (smoother 0 NE, 1 LSGS, 2 sLSGS) on one level in one
+// launch of cs blocks (cs = 1: a single block; else one cluster)
+template <typename T>
+cudaError_t launch_smooth_strips(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, int cs,
+                                 cudaStream_t s);
+
+}  // namespace aaomg
