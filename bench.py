@@ -36,6 +36,29 @@ UNIT = "unknowns/s"
 SWEEP_BYTES_FP32 = 24  # per node and sweep: read y, lambda, f_y, f_lambda; write y, lambda (4 B each)
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_L{L}.json")
 
+# DRAM bytes (read + written) of one finest-level LSGS step at h = 2^-11 from an
+# ncu capture of the band kernel, valid while the kernel's sources hash to SHA.
+BAND_TRAFFIC = {"level": 11, "bytes": 74_925_056,
+                "sha256": "9df8f87721b06ecc3cb68c7056eb2393160301e6633e2916271199848360056a",
+                "files": ["lsgs_band.cu", "band.h", "lean.cuh", "stencil.cuh", "common.cuh", "pair.cuh"]}
+
+
+def band_traffic(level):
+    """The captured traffic per launch, or None when the level differs or the
+    kernel has changed since the capture."""
+    import hashlib
+
+    if level != BAND_TRAFFIC["level"]:
+        return None
+    h = hashlib.sha256()
+    try:
+        for f in BAND_TRAFFIC["files"]:
+            with open(os.path.join(ROOT, "paper_1502_03917_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return BAND_TRAFFIC["bytes"] if h.hexdigest() == BAND_TRAFFIC["sha256"] else None
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -256,11 +279,36 @@ def run_ours(args, rank, world, local):
     achieved = SWEEP_BYTES_FP32 * N * sweeps / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
     peak = pk["hbm_gbs"] if pk else 6800.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": band_traffic(L),
                 "kernel": "finest-level LSGS smoothing sweep (FP32)",
                 "peak_source": "measured" if pk else "fallback",
                 "sweep_ms": sm_ms / sweeps if sweeps else None,
                 "share_of_step": sm_ms / ms if ms else None}
+
+    # By device time the W-cycle is dominated by the latency-bound one-launch
+    # smoothing calls on level 6 (the top kernel of the ncu launch list): time
+    # them inside one real solve (alpha = 1) with in-graph events around each call.
+    by_time = None
+    LT = 6
+    if not args.profiling_run and L > LT + 1:
+        sp = mg.Solver(L, ALPHAS[0], smoother=args.smoother, precision="fp32_refine", cycle=args.cycle, max_iter=100,
+                       profile=True, profile_level=LT, inner_cycles=args.inner_cycles)
+        fa = sp.rhs_from_yd(yD)
+        xa = torch.zeros_like(fa)
+        sp.solve(fa, xa, tol=args.tol)
+        sp.reset_profile()
+        xa.zero_()
+        sp.solve(fa, xa, tol=args.tol)
+        t_ms, nsw = sp.profile()
+        sp.close()
+        NT = ((1 << LT) + 1) ** 2
+        nu = 2
+        if nsw:
+            call_us = t_ms * 1e3 / (nsw / nu)
+            ach = SWEEP_BYTES_FP32 * NT * nsw / (t_ms * 1e-3) / 1e9
+            by_time = {"kernel": f"level-{LT} smoothing call ({(1 << LT) + 1}^2 nodes, {nu} LSGS steps, one block)",
+                       "bound": "latency", "us_per_call": call_us, "us_per_step": call_us / nu,
+                       "achieved": ach, "unit": "GB/s", "frac_of_hbm": ach / peak, "calls_timed": nsw // nu}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -274,7 +322,7 @@ def run_ours(args, rank, world, local):
                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
                       "concurrency": 1 if args.serial else len(ALPHAS)},
            "iterations": {str(a): its32[a] for a in ALPHAS},
-           "roofline": roofline, "clocks": clocks, "gpu_launches": launches}
+           "roofline": roofline, "roofline_by_time": by_time, "clocks": clocks, "gpu_launches": launches}
 
     if not args.no_fp64:
         sol64 = make("fp64", False)

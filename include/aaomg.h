@@ -87,7 +87,8 @@ typedef struct mg_options {
     int max_iter;     /* mg_solve iteration cap; <= 0: 100 */
     int inner_cycles; /* FP32_REFINE: FP32 cycles per refinement step; <= 0: 3 */
     int coarse_level; /* levels <= this run inside one single-block kernel; < 0: default, 0: none */
-    int profile;      /* 1: time the finest-level smoothing inside every iteration (CUDA events) */
+    int profile;      /* 1: time the smoothing calls of one level (profile_level) inside every
+                         iteration (CUDA events) */
     int tile_w;       /* LSGS step kernel: owned columns per block; <= 0: widest the block allows */
     int tile_h;       /* LSGS step kernel: owned rows per block; <= 0: chosen to fill the GPU */
     int small_max;    /* levels with at most this many nodes per side smooth in one launch per
@@ -96,6 +97,8 @@ typedef struct mg_options {
                          side (2..16); 0: by level size and precision (FP32: one block, 8, 16;
                          FP64: 8, 16, 16); 1: one block where it fits, else a launch per colour
                          phase.  A size that cannot run: BAD_ARG */
+    int profile_level; /* with profile = 1: the level whose smoothing calls are timed; <= 0 or
+                          > levels: the finest */
 } mg_options;
 
 /* Build the hierarchy for h = 2^-levels (1 <= levels <= 13; level 1 is the
@@ -181,10 +184,11 @@ AAOMG_API int mg_adjoint(mg_handle h, const double* x, const double* ubar, doubl
  * initial one; *n receives the count written (<= cap). */
 AAOMG_API int mg_get_history(mg_handle h, double* buf, int cap, int* n);
 
-/* With opt.profile = 1: total device time (ms) of the finest-level smoothing
- * steps inside the iterations run since the last mg_reset_profile, and the
- * number of smoothing steps (sweeps) it covers; measured with CUDA events on
- * the stream the kernels run on. */
+/* With opt.profile = 1: total device time (ms) of the smoothing calls on the
+ * profiled level (opt.profile_level, default the finest) inside the iterations
+ * run since the last mg_reset_profile, and the number of smoothing steps
+ * (sweeps) they cover; measured with CUDA events on the stream the kernels run
+ * on. */
 AAOMG_API int mg_get_profile(mg_handle h, double* smooth_ms, long long* sweeps);
 AAOMG_API int mg_reset_profile(mg_handle h);
 

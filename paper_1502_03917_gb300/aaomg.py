@@ -50,6 +50,7 @@ class Options(ctypes.Structure):
         ("tile_h", ctypes.c_int),
         ("small_max", ctypes.c_int),
         ("cluster_size", ctypes.c_int),
+        ("profile_level", ctypes.c_int),
     ]
 
 
@@ -160,13 +161,15 @@ class Solver:
     def __init__(self, levels: int, alpha: float, smoother: str = "lsgs", precision: str = "fp64",
                  cycle: str = "W", nu_pre: int = 0, nu_post: int = 0, tau: float = 0.0, k_variant: int = 0,
                  max_iter: int = 0, inner_cycles: int = 0, coarse_level: int = -1, profile: bool = False,
-                 tile_w: int = 0, tile_h: int = 0, small_max: int = 0, cluster_size: int = 0):
+                 tile_w: int = 0, tile_h: int = 0, small_max: int = 0, cluster_size: int = 0,
+                 profile_level: int = 0):
         self._lib = load()
         self.levels, self.alpha = int(levels), float(alpha)
         self.smoother, self.precision, self.cycle_kind = smoother, precision, cycle
         opt = Options(SMOOTHER[smoother], int(nu_pre), int(nu_post), CYCLE[cycle], PRECISION[precision],
                       float(tau), int(k_variant), int(max_iter), int(inner_cycles), int(coarse_level),
-                      int(bool(profile)), int(tile_w), int(tile_h), int(small_max), int(cluster_size))
+                      int(bool(profile)), int(tile_w), int(tile_h), int(small_max), int(cluster_size),
+                      int(profile_level))
         h = ctypes.c_void_p()
         _check(self._lib.mg_setup(self.levels, self.alpha, ctypes.byref(opt), ctypes.byref(h)), "mg_setup")
         self._h = h
@@ -278,8 +281,9 @@ class Solver:
         return [buf[i] for i in range(n.value)]
 
     def profile(self):
-        """(ms, sweeps): device time of the finest-level smoothing inside the
-        iterations since the last reset, and the sweeps it covers."""
+        """(ms, sweeps): device time of the smoothing calls on the profiled
+        level (the finest unless profile_level is set) inside the iterations
+        since the last reset, and the sweeps they cover."""
         ms, sw = ctypes.c_double(), ctypes.c_longlong()
         _check(self._lib.mg_get_profile(self._h, ctypes.byref(ms), ctypes.byref(sw)), "mg_get_profile")
         return ms.value, sw.value

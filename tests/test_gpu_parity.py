@@ -256,6 +256,20 @@ def test_solve_host_and_history(mg, oracle_mod):
         np.testing.assert_allclose(h, hist_o, rtol=1e-7, atol=1e-14)
 
 
+def test_profile_of_one_level(mg):
+    """profile_level times the smoothing calls of that level: a W-cycle from
+    level 8 visits level 6 four times, with nu_pre + nu_post = 4 steps a visit,
+    in each of the inner cycles of every refinement step."""
+    L = 8
+    with mg.Solver(L, 1e-2, smoother="lsgs", precision="fp32_refine", profile=True, profile_level=6) as s:
+        f = s.rhs_from_yd(dev(inputs.yd_sine_noise(L, 1)))
+        x = torch.zeros_like(f)
+        it, rr, code = s.solve(f, x, tol=1e-6)
+        ms, sweeps = s.profile()
+        assert code == 0 and ms > 0.0
+        assert sweeps == it * 3 * 4 * 4
+
+
 def test_determinism(mg):
     L, alpha = 6, 1e-4
     yD = dev(inputs.yd_uniform(L, 3))
