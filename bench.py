@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--level", type=int, default=11)
     p.add_argument("--tol", type=float, default=1e-8)
-    p.add_argument("--smoother", default="lsgs", choices=["ne", "lsgs", "slsgs"])
+    p.add_argument("--smoother", default="lsgs", choices=["ne", "lsgs", "slsgs", "cgs"])
     p.add_argument("--cycle", default="W", choices=["V", "W"])
     p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison")
     p.add_argument("--no-e2e", action="store_true")

@@ -20,7 +20,8 @@
  * the canonical embedding, recursive coarse correction, prolongation,
  * post-smoothing; exact solve on the coarsest grid h = 1/2), with the
  * normal-equation smoother (Algorithm 1), the least-squares Gauss-Seidel
- * smoother LSGS (Algorithm 2) or its symmetric form sLSGS.
+ * smoother LSGS (Algorithm 2), its symmetric form sLSGS, or the collective
+ * Gauss-Seidel smoother CGS.
  *
  * Vectors.  A grid level with n = 2^k cells per side has N = (n+1)^2 nodes;
  * node (i h, j h), 0 <= i, j <= n, has index j*(n+1) + i.  Every vector passed
@@ -68,6 +69,8 @@ extern "C" {
 #define MG_SMOOTHER_NE 0    /* normal equation smoother, Algorithm 1, damped by tau */
 #define MG_SMOOTHER_LSGS 1  /* least-squares Gauss-Seidel, Algorithm 2, undamped */
 #define MG_SMOOTHER_SLSGS 2 /* symmetric LSGS: LSGS step then LSGS step in reversed order */
+#define MG_SMOOTHER_CGS 3   /* collective Gauss-Seidel: the 2x2 block (y_i, lambda_i) of each node
+                               solved in turn, nodes in the colour order (i + j) mod 3 */
 
 /* precision */
 #define MG_PREC_FP64 0        /* every operation in FP64 */

@@ -17,7 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libaaomg.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "aaomg.h")
 
-SMOOTHER = {"ne": 0, "lsgs": 1, "slsgs": 2}
+SMOOTHER = {"ne": 0, "lsgs": 1, "slsgs": 2, "cgs": 3}
 PRECISION = {"fp64": 0, "fp32_refine": 1}
 CYCLE = {"V": 1, "W": 2}
 

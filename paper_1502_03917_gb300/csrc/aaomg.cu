@@ -289,12 +289,17 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* rh = (T*)v.rh;
     if (v.cs > 0) {
         // the whole smoothing call in one launch of one block or one cluster
-        // (x and rh in shared memory)
+        // (x and rh, or for CGS x and f, in shared memory)
         launch_smooth_strips<T>(P, H->o.smoother, steps, x, f, v.cs, s);
         H->rec_kernels += 1;
         return;
     }
     switch (H->o.smoother) {
+    case MG_SMOOTHER_CGS:
+        for (int m = 0; m < steps; ++m)
+            for (int c = 0; c < 3; ++c) launch_cgs_phase<T>(P, c, f, x, s);
+        H->rec_kernels += 3 * steps;
+        break;
     case MG_SMOOTHER_NE:
         for (int m = 0; m < steps; ++m) {
             launch_resid_hat<T>(P, f, x, rh, s);
@@ -621,7 +626,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
     if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(AAOMG_ERR_BAD_ARG, "alpha must be positive and finite");
     mg_options o{};
     if (opt) o = *opt;
-    if (o.smoother < 0 || o.smoother > MG_SMOOTHER_SLSGS) return fail(AAOMG_ERR_BAD_ARG, "unknown smoother");
+    if (o.smoother < 0 || o.smoother > MG_SMOOTHER_CGS) return fail(AAOMG_ERR_BAD_ARG, "unknown smoother");
     if (o.precision < 0 || o.precision > MG_PREC_FP32_REFINE) return fail(AAOMG_ERR_BAD_ARG, "unknown precision");
     if (o.cycle < 0 || o.cycle > 2) return fail(AAOMG_ERR_BAD_ARG, "cycle must be 1 (V) or 2 (W)");
     if (o.k_variant < 0 || o.k_variant > 1) return fail(AAOMG_ERR_BAD_ARG, "k_variant must be 0 or 1");

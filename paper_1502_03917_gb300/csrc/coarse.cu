@@ -45,11 +45,28 @@ __device__ void cta_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, 
 }
 
 template <typename T>
+__device__ void cta_cgs_phase(const LevelP<T>& P, int colour, const T* f, T* x) {
+    const int n1 = P.n + 1;
+    const int spr = (n1 + 2) / 3;  // nodes of one colour per row (at most)
+    for (int t = threadIdx.x; t < n1 * spr; t += blockDim.x) {
+        int j = t / spr, k = t - j * spr;
+        int i = ((colour - j) % 3 + 3) % 3 + 3 * k;
+        if (i <= P.n) cgs_update_at(P, f, x, i, j);
+    }
+    __syncthreads();
+}
+
+template <typename T>
 __device__ void cta_smooth(const CtaParams<T>& C, const CtaState<T>& S, int l, int steps) {
     if (steps <= 0) return;
     const LevelP<T>& P = C.P[l];
     const int n1 = P.n + 1, nn = n1 * n1;
     T *x = S.x[l], *f = S.f[l], *rh = S.rh[l];
+    if (C.smoother == 3) {
+        for (int m = 0; m < steps; ++m)
+            for (int c = 0; c < 3; ++c) cta_cgs_phase(P, c, f, x);
+        return;
+    }
     if (C.smoother == 0) {
         for (int m = 0; m < steps; ++m) {
             for (int t = threadIdx.x; t < nn; t += blockDim.x) resid_hat_at(P, f, x, rh, t % n1, t / n1);

@@ -82,6 +82,20 @@ __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__
     }
 }
 
+// One colour phase of the CGS smoother: every node of colour c of (i + j) mod 3
+// (no two coupled) solves its 2x2 block against the residual of the current
+// iterate.  One thread per slot; slot t is row t / spr, the k-th node of the
+// colour in that row.
+template <typename T>
+__global__ void k_cgs_phase(LevelP<T> P, int colour, const T* __restrict__ f, T* __restrict__ x) {
+    const int spr = (P.n + 1 + 2) / 3;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (P.n + 1) * spr) return;
+    const int j = t / spr, k = t - j * spr;
+    const int i = ((colour - j) % 3 + 3) % 3 + 3 * k;
+    if (i <= P.n) cgs_update_at(P, f, x, i, j);
+}
+
 // Defect restriction: fc = P^T (f - A x) on a coarse node (I,J) -- weight 1 at
 // the fine node (2I,2J) and 1/2 at its six neighbours, the midpoints of the
 // coarse edges; also zeroes the coarse iterate xc.
@@ -301,6 +315,11 @@ void launch_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, T* rh, c
 #undef L_
 }
 template <typename T>
+void launch_cgs_phase(const LevelP<T>& P, int colour, const T* f, T* x, cudaStream_t s) {
+    const int slots = (P.n + 1) * ((P.n + 1 + 2) / 3);
+    k_cgs_phase<T><<<(slots + 255) / 256, 256, 0, s>>>(P, colour, f, x);
+}
+template <typename T>
 void launch_restrict(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* f, const T* x, T* fc, T* xc, cudaStream_t s) {
     k_restrict<T><<<grid2(Pc.n + 1, Pc.n + 1, kBlk2), kBlk2, 0, s>>>(Pf, Pc, f, x, fc, xc);
 }
@@ -338,6 +357,7 @@ void launch_rhs(const LevelP<double>& P, const double* yD, double* f, cudaStream
     template void launch_resid_hat<T>(const LevelP<T>&, const T*, const T*, T*, cudaStream_t);                \
     template void launch_ne_update<T>(const LevelP<T>&, T*, const T*, cudaStream_t);                          \
     template void launch_lsgs_phase<T>(const LevelP<T>&, int, int, T*, T*, cudaStream_t);                     \
+    template void launch_cgs_phase<T>(const LevelP<T>&, int, const T*, T*, cudaStream_t);                      \
     template void launch_restrict<T>(const LevelP<T>&, const LevelP<T>&, const T*, const T*, T*, T*,          \
                                      cudaStream_t);                                                           \
     template void launch_prolong<T>(const LevelP<T>&, const LevelP<T>&, const T*, T*, cudaStream_t);          \

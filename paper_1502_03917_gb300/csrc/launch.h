@@ -12,6 +12,9 @@ template <typename T>
 void launch_ne_update(const LevelP<T>& P, T* x, const T* rh, cudaStream_t s);
 template <typename T>
 void launch_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, T* rh, cudaStream_t s);
+// one colour phase (colour of (i + j) mod 3) of the CGS smoother, in place on x
+template <typename T>
+void launch_cgs_phase(const LevelP<T>& P, int colour, const T* f, T* x, cudaStream_t s);
 template <typename T>
 void launch_restrict(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* f, const T* x, T* fc, T* xc, cudaStream_t s);
 template <typename T>

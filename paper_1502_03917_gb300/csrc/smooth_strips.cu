@@ -166,21 +166,23 @@ __device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass
 
 // Edge nodes of a strip, enumerated per pass: the strip's full boundary rows
 // (rows 0, 1 in the first block, n-1, n in the last) slot by slot, then the
-// columns 0, 1, n-1, n of its other rows.  For one colour c the nodes of column
-// i sit in the rows j = 4 (c - i) mod 7 (2 j = c - i mod 7), every 7th row, so
-// each column gets ceil(rows / 7) slots; c < 0 (every colour): every row.
-template <int N>
+// columns 0, 1, n-1, n of its other rows.  Colour c of node (i, j) is
+// (i + A j) mod K (LSGS: A = 2, K = 7; CGS: A = 1, K = 3); in column i the
+// nodes of colour c sit in the rows j = AINV (c - i) mod K (AINV = A^-1 mod K),
+// every K-th row, so each column gets ceil(rows / K) slots; c < 0 (every
+// colour): every row.
+template <int N, int K = 7, int A = 2, int AINV = 4>
 struct StripEdges {
-    static constexpr int FPR = (N + 1 + 6) / 7;  // slots of one colour per full row
+    static constexpr int FPR = (N + 1 + K - 1) / K;  // slots of one colour per full row
     int nfull, first_full_hi, ja, nrows;
-    __device__ __forceinline__ int per_col(int c) const { return c < 0 ? nrows : (nrows + 6) / 7; }
+    __device__ __forceinline__ int per_col(int c) const { return c < 0 ? nrows : (nrows + K - 1) / K; }
     __device__ __forceinline__ int count(int c) const { return nfull * (c < 0 ? N + 1 : FPR) + 4 * per_col(c); }
     __device__ __forceinline__ bool node(int t, int c, int& i, int& j) const {
         const int per = c < 0 ? N + 1 : FPR;
         if (t < nfull * per) {
             const int r = t / per, k = t - r * per;
             j = r < first_full_hi ? r : N - 1 + (r - first_full_hi);
-            i = c < 0 ? k : ((c - 2 * j) % 7 + 7) % 7 + 7 * k;
+            i = c < 0 ? k : ((c - A * j) % K + K) % K + K * k;
             return i <= N;
         }
         t -= nfull * per;
@@ -191,10 +193,39 @@ struct StripEdges {
             ++q;
         }
         i = q < 2 ? q : N - 3 + q;
-        j = c < 0 ? ja + k : ja + ((4 * (c - i) - ja) % 7 + 7) % 7 + 7 * k;
+        j = c < 0 ? ja + k : ja + ((AINV * (c - i) - ja) % K + K) % K + K * k;
         return j < ja + nrows;
     }
 };
+
+// ----------------------------------------------------------------- CGS --
+// Collective Gauss-Seidel update of node (i,j): the residual of its two rows
+// from the current iterate (x rows) and its (f_y, f_lambda), then the 2x2
+// diagonal block solve; the deep-interior block is constant.
+template <typename T, typename V2>
+__device__ __forceinline__ void rows_cgs_fast(const LevelP<T>& P, V2* xs, const V2* xsp, const V2* xsm, int i,
+                                              V2 fv) {
+    V2 M, K, nb[7];
+    rows_stencil(xs, xsp, xsm, i, psplat(P.mC), psplat(P.mO), M, K, nb);
+    T ay, al, dy, dl;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, ay, al);
+    cgs_block(P, P.mC, T(4) + P.km * P.mC, fv.x - ay, fv.y - al, dy, dl);
+    xs[i] = pmake<T>(nb[0].x + dy, nb[0].y + dl);
+}
+
+template <typename T, int N, class S_>
+__device__ __forceinline__ void cl_cgs_edge(const LevelP<T>& P, const EdgeClass<T>& C, const S_& S,
+                                            const typename P2<T>::t* F, int i, int j) {
+    using V2 = typename P2<T>::t;
+    V2* const rows[3] = {S.xrow(j - 1), S.xrow(j), S.xrow(j + 1)};
+    V2 v[7];
+    T My, Ky, Ml, Kl, ay, al, dy, dl;
+    cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
+    const V2 fv = F[(j - S.r0) * (N + 1) + i];
+    cgs_block(P, C.m[0], C.kd[0] + P.km * C.m[0], fv.x - ay, fv.y - al, dy, dl);
+    rows[1][i] = pmake<T>(v[0].x + dy, v[0].y + dl);
+}
 
 // ------------------------------------------------------------- kernel --
 // Deep-interior nodes of the strip (rows and columns 2..N-2; warp-rounded
@@ -295,7 +326,36 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
         barrier();
     };
 
-    if (smoother == 0) {
+    if (smoother == 3) {
+        // CGS keeps no residual: R holds the strip's (f_y, f_lambda) pairs
+        for (int t = g; t < nown; t += G) R[t] = pmake<T>(f[base + t], f[base + t + P.fs]);
+        __syncthreads();
+        constexpr int CPR3 = (N - 3 + 2) / 3;  // deep-interior slots per row of one colour
+        StripEdges<N, 3, 1, 1> SE3;
+        SE3.first_full_hi = SE.first_full_hi;
+        SE3.nfull = SE.nfull;
+        SE3.ja = ja;
+        SE3.nrows = nrows;
+        for (int m = 0; m < steps; ++m)
+            for (int c = 0; c < 3; ++c) {
+                const int ni = nrows * CPR3, nip = (ni + 31) & ~31;
+                const int ne = SE3.count(c);
+                for (int t = g; t < nip + ne; t += G) {
+                    if (t < nip) {
+                        if (t < ni) {
+                            const int r = t / CPR3, k = t - r * CPR3, j = ja + r;
+                            const int i = 2 + ((c - j - 2) % 3 + 3) % 3 + 3 * k;
+                            if (i <= N - 2)
+                                rows_cgs_fast<T>(P, S.xrow(j), S.xrow(j + 1), S.xrow(j - 1), i, R[(j - S.r0) * LD + i]);
+                        }
+                    } else {
+                        int i, j;
+                        if (SE3.node(t - nip, c, i, j)) cl_cgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], S, R, i, j);
+                    }
+                }
+                barrier();
+            }
+    } else if (smoother == 0) {
         for (int m = 0; m < steps; ++m) {
             resid_all();
             for (int t = g; t < niap + nea; t += G) {

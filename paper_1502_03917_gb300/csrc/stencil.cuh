@@ -201,6 +201,32 @@ __device__ __forceinline__ void lsgs_update_acc(const LevelP<T>& P, int field, T
     }
 }
 
+// Collective Gauss-Seidel (section 2, the point block smoother): solve the 2x2
+// diagonal block [[m, c k], [c k, -d m]] of node i (m = M_ii, k = K_ii) for the
+// residual (ry, rl) of its two rows and return the correction.
+template <typename T>
+__device__ __forceinline__ void cgs_block(const LevelP<T>& P, T m, T k, T ry, T rl, T& dy, T& dl) {
+    const T ck = P.c * k;
+    const T det = -(P.d * m * m + ck * ck);
+    dy = (-P.d * m * ry - ck * rl) / det;
+    dl = (m * rl - ck * ry) / det;
+}
+
+// one CGS update of node (i,j): the residual of its two rows from the current
+// iterate (nodes of one colour of (i + j) mod 3 are not coupled, so the
+// updates of a colour are independent), then the block solve
+template <typename T>
+__device__ __forceinline__ void cgs_update_at(const LevelP<T>& P, const T* f, T* x, int i, int j) {
+    T ay, al, m[7], kd[7];
+    apply_A(P, x, i, j, ay, al);
+    row_coeffs(P, i, j, m, kd);
+    const int64_t p = nidx(P, i, j);
+    T dy, dl;
+    cgs_block(P, m[0], kd[0] + P.km * m[0], f[p] - ay, f[p + P.fs] - al, dy, dl);
+    x[p] += dy;
+    x[p + P.fs] += dl;
+}
+
 // the same with the two fields of rh apart (field stride P.fs)
 template <typename T>
 __device__ __forceinline__ void resid_hat_at(const LevelP<T>& P, const T* f, const T* x, T* rh, int i, int j) {

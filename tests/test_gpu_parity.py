@@ -44,7 +44,7 @@ def field_reldiff(a, b, n):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs", "cgs"])
 @pytest.mark.parametrize("L", [2, 3, 5, 7, 9])
 @pytest.mark.parametrize("alpha", [1.0, 1e-4, 1e-8])
 def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
@@ -63,7 +63,7 @@ def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs", "cgs"])
 @pytest.mark.parametrize("L,small_max", [(6, 0), (8, 0), (10, 0), (6, -1), (8, -1), (9, 300)])
 def test_smoothing_call_kernels(mg, oracle_mod, L, small_max, smoother, precision):
     """The one-launch smoothing call (one block with the residual in shared
@@ -83,7 +83,7 @@ def test_smoothing_call_kernels(mg, oracle_mod, L, small_max, smoother, precisio
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs", "cgs"])
 @pytest.mark.parametrize("L,cs", [(6, 2), (6, 3), (6, 16), (7, 5), (7, 16), (8, 12), (8, 16)])
 def test_cluster_smoothing_call(mg, oracle_mod, L, cs, smoother, precision):
     """The one-launch smoothing call on a cluster of cs blocks (grid rows split
@@ -168,11 +168,16 @@ def test_residual_and_rhs_parity(mg, oracle_mod, L):
 
 @pytest.mark.parametrize("coarse_level", [-1, 0, 3])
 @pytest.mark.parametrize("cycle", ["W", "V"])
-@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs", "cgs"])
 @pytest.mark.parametrize("L", [1, 2, 4, 7])
 def test_cycle_parity_fp64(mg, oracle_mod, L, smoother, cycle, coarse_level):
     """coarse_level -1: default single-block coarse kernel (levels <= 5 in
-    FP64); 0: grid-wide kernels on every level; 3: a mix."""
+    FP64); 0: grid-wide kernels on every level; 3: a mix.  Per sweep the two
+    sides differ by summation order only (1e-12); a cycle then solves the
+    coarse problem from a defect carrying that rounding, which the condition
+    number of the operator, O(h^-2) = O(4^L), amplifies: tol = max(1e-12,
+    2^-52 4^L) (CGS recomputes each node's residual where the oracle carries
+    it, which shows this at L = 7)."""
     alpha = 1e-2
     nu = 1 if smoother == "slsgs" else 2
     o = oracle_mod.Oracle(L, alpha, smoother=smoother, gamma=2 if cycle == "W" else 1, nu_pre=nu, nu_post=nu)
@@ -182,11 +187,11 @@ def test_cycle_parity_fp64(mg, oracle_mod, L, smoother, cycle, coarse_level):
         x = dev(x0)
         s.cycle(dev(f), x)
         want = o.cycle(f, x0)
-        assert field_reldiff(host(x), want, o.nn()) <= 1e-12
+        assert field_reldiff(host(x), want, o.nn()) <= max(1e-12, 2.0 ** -52 * 4.0 ** L)
 
 
 @pytest.mark.parametrize("coarse_level", [-1, 0])
-@pytest.mark.parametrize("smoother", ["ne", "lsgs"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "cgs"])
 @pytest.mark.parametrize("L", [3, 6, 8])
 def test_refinement_step_parity_fp32(mg, oracle_mod, L, smoother, coarse_level):
     """One FP32 cycle inside the refinement step: its correction matches one
@@ -220,7 +225,7 @@ def solution_errors(o, x, xo):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
-@pytest.mark.parametrize("smoother", ["ne", "lsgs"])
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "cgs"])
 @pytest.mark.parametrize("alpha", [1.0, 1e-2, 1e-4, 1e-6, 1e-8])
 def test_solve_parity_L5(mg, oracle_mod, alpha, smoother, precision):
     L = 5
