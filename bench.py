@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-vcycle", action="store_true", help="skip the V-cycle comparison")
     p.add_argument("--inner-cycles", type=int, default=0, help="FP32 cycles per refinement step (0: library default)")
+    p.add_argument("--protocol", action="store_true",
+                   help="print the iteration counts of the paper's protocol (Table 1 layout) instead of timing")
     p.add_argument("--profiling-run", action="store_true",
                    help="for runs under an external profiler: no CUDA events inside the solver graphs and no "
                         "nvidia-smi sampling (roofline and clocks are then not reported)")
@@ -488,10 +490,49 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_protocol(args):
+    """Section 3's protocol on the GPU, laid out like Table 1: zero right-hand
+    side, random start U(-1,1) (seed 7), W-cycles with 2+2 steps (sLSGS 1+1)
+    until the error in the L norm has dropped by 1e-6, for k = 5..8 and
+    alpha in {1, 1e-6, 1e-12}.  Counts in FP64 and with one FP32 cycle per
+    refinement step, beside the paper's (natural order of Algorithm 2; the GPU
+    visits the unknowns in the multicolour order)."""
+    import torch
+
+    from paper_1502_03917_gb300 import build as B
+    from paper_1502_03917_gb300 import inputs
+    import paper_1502_03917_gb300.aaomg as mg
+
+    B.build()
+    paper = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table1_iterations.txt")) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) == 4 and not line.startswith("#"):
+                paper[(parts[0], int(parts[1]), float(parts[2]))] = int(parts[3])
+    rows = []
+    t0 = time.time()
+    for sm in ("ne", "lsgs", "slsgs", "cgs"):
+        nu = 1 if sm == "slsgs" else 2
+        for k in (5, 6, 7, 8):
+            x0 = torch.tensor(inputs.x_uniform(k, 7), dtype=torch.float64, device="cuda")
+            for a in (1.0, 1e-6, 1e-12):
+                row = {"smoother": sm, "k": k, "alpha": a, "paper": paper.get((sm, k, a))}
+                for prec in ("fp64", "fp32_refine"):
+                    with mg.Solver(k, a, smoother=sm, precision=prec, nu_pre=nu, nu_post=nu, inner_cycles=1) as s:
+                        row[prec] = s.protocol_iterations(x0, 1e-6, 300)
+                rows.append(row)
+    print(json.dumps({"protocol": "section 3 (Table 1 layout), W-cycle, coarsest h = 1/2, multicolour order",
+                      "seconds": time.time() - t0, "rows": rows}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.impl == "reference":
+    if args.protocol:
+        if rank == 0:
+            run_protocol(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local)

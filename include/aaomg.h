@@ -183,6 +183,13 @@ AAOMG_API int mg_control(mg_handle h, const double* x, double* u, void* stream);
 AAOMG_API int mg_adjoint(mg_handle h, const double* x, const double* ubar, double* z, double* gyD, double* dalpha,
                          double tol, void* stream);
 
+/* ||x||_L and ||x||_{L^-1} of a vector x (2N doubles, device) on the finest
+ * level, with L = diag(Q) of the paper's block preconditioner (section 2):
+ * L_y = diag(M + alpha^{1/2} K), L_lambda = alpha^{-1} L_y.  ||.||_L is the norm
+ * in which section 3 measures the error.  Either output may be NULL (not
+ * both); results are written on the host after the stream has finished. */
+AAOMG_API int mg_norms(mg_handle h, const double* x, double* norm_L, double* norm_Linv, void* stream);
+
 /* Relative residual after each iteration of the last mg_solve: buf[0] is the
  * initial one; *n receives the count written (<= cap). */
 AAOMG_API int mg_get_history(mg_handle h, double* buf, int cap, int* n);

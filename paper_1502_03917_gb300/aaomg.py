@@ -85,6 +85,7 @@ def load():
             "mg_solve": (I, [H, P, P, D, pI, pD, P]),
             "mg_solve_host": (I, [H, P, P, D, pI, pD, P]),
             "mg_get_history": (I, [H, pD, I, pI]),
+            "mg_norms": (I, [H, P, pD, pD, P]),
             "mg_kernel_launches": (ctypes.c_longlong, [H]),
             "mg_get_profile": (I, [H, pD, ctypes.POINTER(ctypes.c_longlong)]),
             "mg_reset_profile": (I, [H]),
@@ -237,6 +238,29 @@ class Solver:
         if raise_on_fail:
             _check(code, "mg_solve")
         return it.value, rr.value, code
+
+    def norms(self, x):
+        """(||x||_L, ||x||_{L^-1}) on the finest level (the paper's L = diag(Q))."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.mg_norms(self._h, _dptr(x, 2 * self.N), ctypes.byref(a), ctypes.byref(b), _stream()),
+               "mg_norms")
+        return a.value, b.value
+
+    def protocol_iterations(self, x0, reduction: float = 1e-6, max_iter: int = 300) -> int:
+        """Section 3's protocol: zero right-hand side, start x0 (not modified),
+        cycles until ||x||_L has dropped by `reduction`; -1 if max_iter is hit."""
+        import torch
+
+        x = x0.clone()
+        f = torch.zeros_like(x)
+        e0 = self.norms(x)[0]
+        it = 0
+        while self.norms(x)[0] > reduction * e0:
+            if it >= max_iter:
+                return -1
+            self.cycle(f, x)
+            it += 1
+        return it
 
     def solve_host(self, f, x, tol: float = 1e-8, raise_on_fail: bool = True):
         """f, x: C-contiguous float64 numpy arrays (x in/out) in host memory."""

@@ -831,6 +831,21 @@ int mg_residual(mg_handle h, const double* f, const double* x, double* r, double
     return AAOMG_OK;
 }
 
+int mg_norms(mg_handle h, const double* x, double* norm_L, double* norm_Linv, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x || (!norm_L && !norm_Linv)) return fail(AAOMG_ERR_BAD_ARG, "null vector or no output");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_norms64(h->fine64, x, h->part, kResidBlocks, h->red, s);
+    h->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_red, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (norm_L) *norm_L = std::sqrt(h->h_red[0]);
+    if (norm_Linv) *norm_Linv = std::sqrt(h->h_red[1]);
+    return AAOMG_OK;
+}
+
 int mg_smooth(mg_handle h, const double* f, double* x, int steps, void* stream) {
     int rc = check_handle(h);
     if (rc) return rc;

@@ -205,6 +205,25 @@ __global__ void k_resid64(LevelP<double> P, const double* __restrict__ f, const 
     }
 }
 
+// ||x||^2_L and ||x||^2_{L^-1} partial sums per block, L = diag(Q) of the
+// paper's system: L_y = M_ii + alpha^{1/2} K_ii, L_lambda = alpha^{-1} L_y
+__global__ void k_norms64(LevelP<double> P, const double* __restrict__ x, double* __restrict__ part) {
+    int64_t nn = (int64_t)(P.n + 1) * (P.n + 1);
+    double sl = 0.0, sinv = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(t / (P.n + 1)), i = (int)(t - (int64_t)j * (P.n + 1));
+        int64_t p = nidx(P, i, j);
+        double il = inv_ly(P, i, j), xy = x[p], xl = x[p + P.fs];
+        sl += xy * xy / il + xl * xl * (P.d / il);
+        sinv += xy * xy * il + xl * xl * (il * P.invd);
+    }
+    block_sum2(sl, sinv);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sl;
+        part[2 * blockIdx.x + 1] = sinv;
+    }
+}
+
 // sum the per-block partials in a fixed order (deterministic)
 __global__ void k_reduce_parts(const double* __restrict__ part, int nblk, double* __restrict__ out) {
     double a = 0.0, b = 0.0;
@@ -335,6 +354,10 @@ void launch_coarsest(const double* ainv, const T* f, T* x, int64_t fs, cudaStrea
 void launch_resid64(const LevelP<double>& P, const double* f, const double* x, double* r, float* fin, int64_t fin_ld,
                     int64_t fin_fs, double* part, int nblk, double* out, cudaStream_t s) {
     k_resid64<<<nblk, 256, 0, s>>>(P, f, x, r, fin, fin_ld, fin_fs, part);
+    k_reduce_parts<<<1, 256, 0, s>>>(part, nblk, out);
+}
+void launch_norms64(const LevelP<double>& P, const double* x, double* part, int nblk, double* out, cudaStream_t s) {
+    k_norms64<<<nblk, 256, 0, s>>>(P, x, part);
     k_reduce_parts<<<1, 256, 0, s>>>(part, nblk, out);
 }
 void launch_refine_update(const LevelP<double>& P, double* x, const float* d, int64_t d_ld, int64_t d_fs,

@@ -26,6 +26,8 @@ void launch_coarsest(const double* ainv, const T* f, T* x, int64_t fs, cudaStrea
 // out[0] = ||f - A x||^2_{L^-1}, out[1] = ||f||^2_{L^-1} (device).
 void launch_resid64(const LevelP<double>& P, const double* f, const double* x, double* r, float* fin, int64_t fin_ld,
                     int64_t fin_fs, double* part, int nblk, double* out, cudaStream_t s);
+// out[0] = ||x||^2_L, out[1] = ||x||^2_{L^-1} on the paper's system (device)
+void launch_norms64(const LevelP<double>& P, const double* x, double* part, int nblk, double* out, cudaStream_t s);
 void launch_refine_update(const LevelP<double>& P, double* x, const float* d, int64_t d_ld, int64_t d_fs,
                           cudaStream_t s);
 void launch_to_f32(int n, const double* v, int64_t v_ld, int64_t v_fs, float* out, int64_t o_ld, int64_t o_fs,

@@ -261,6 +261,36 @@ def test_solve_host_and_history(mg, oracle_mod):
         np.testing.assert_allclose(h, hist_o, rtol=1e-7, atol=1e-14)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("alpha", [1.0, 1e-6])
+def test_norms_match_oracle(mg, oracle_mod, alpha, precision):
+    """mg_norms: ||x||_L and ||x||_{L^-1} with the paper's L = diag(Q)."""
+    L = 5
+    o = oracle_mod.Oracle(L, alpha)
+    x0 = inputs.x_uniform(L, 11)
+    with mg.Solver(L, alpha, precision=precision) as s:
+        nl, ninv = s.norms(dev(x0))
+    assert nl == pytest.approx(o.norm_L(x0), rel=1e-13)
+    assert ninv == pytest.approx(o.norm_Linv(x0), rel=1e-13)
+
+
+@pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs", "cgs"])
+@pytest.mark.parametrize("k", [5, 6])
+@pytest.mark.parametrize("alpha", [1.0, 1e-6, 1e-12])
+def test_protocol_iterations_match_oracle(mg, oracle_mod, k, alpha, smoother):
+    """Section 3's protocol (zero right-hand side, random start, W-cycles until
+    the error in the L norm has dropped by 1e-6; 2+2 steps, sLSGS 1+1) on the
+    GPU in FP64 takes exactly the oracle's iteration count in the same colour
+    order: the iterates agree to rounding."""
+    nu = 1 if smoother == "slsgs" else 2
+    o = oracle_mod.Oracle(k, alpha, smoother=smoother, nu_pre=nu, nu_post=nu)
+    x0 = inputs.x_uniform(k, 7)
+    want = o.protocol_iterations(x0, 1e-6, 300)
+    with mg.Solver(k, alpha, smoother=smoother, precision="fp64", nu_pre=nu, nu_post=nu) as s:
+        got = s.protocol_iterations(dev(x0), 1e-6, 300)
+    assert got == want > 0
+
+
 def test_profile_of_one_level(mg):
     """profile_level times the smoothing calls of that level: a W-cycle from
     level 8 visits level 6 four times, with nu_pre + nu_post = 4 steps a visit,
