@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-vcycle", action="store_true", help="skip the V-cycle comparison")
     p.add_argument("--inner-cycles", type=int, default=0, help="FP32 cycles per refinement step (0: library default)")
+    p.add_argument("--batch", type=int, default=0,
+                   help="time N independent instances of mixed size through mg_solve_batch instead")
     p.add_argument("--protocol", action="store_true",
                    help="print the iteration counts of the paper's protocol (Table 1 layout) instead of timing")
     p.add_argument("--profiling-run", action="store_true",
@@ -526,10 +528,65 @@ def run_protocol(args):
                       "seconds": time.time() - t0, "rows": rows}))
 
 
+def run_batch(args):
+    """The batched-solve configuration: independent instances with levels
+    uniform in 6..10, alpha log-uniform in [1e-8, 1], y_D ~ U(-1, 1) (one
+    generator, seed 2), LSGS W(2,2), FP32 cycles in FP64 refinement, all in
+    flight at once through mg_solve_batch; value = unknowns solved per second
+    over all instances (set-up excluded and reported)."""
+    import torch
+
+    from paper_1502_03917_gb300 import build as B
+    from paper_1502_03917_gb300 import inputs
+    import paper_1502_03917_gb300.aaomg as mg
+
+    B.build()
+    levels, alphas, yds = inputs.batch_instances(args.batch, 2)
+    t0 = time.time()
+    solvers = [mg.Solver(L, a, smoother=args.smoother, precision="fp32_refine", cycle=args.cycle, max_iter=100,
+                         inner_cycles=args.inner_cycles) for L, a in zip(levels, alphas)]
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    fs = [s.rhs_from_yd(torch.tensor(y, dtype=torch.float64, device="cuda")) for s, y in zip(solvers, yds)]
+    xs = [torch.zeros_like(f) for f in fs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def step():
+        for x in xs:
+            x.zero_()
+        return mg.solve_batch(solvers, fs, xs, tol=args.tol)
+
+    for _ in range(args.warmup):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    its = None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        its, rrs, code = step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    unknowns = sum(2 * (((1 << L) + 1) ** 2) for L in levels)
+    hist = {}
+    for k in its:
+        hist[str(k)] = hist.get(str(k), 0) + 1
+    print(json.dumps({"metric": "batched solves: unknowns/s at %g rel. residual" % args.tol,
+                      "value": unknowns * args.steps / (ms / 1e3), "unit": UNIT, "instances": args.batch,
+                      "unknowns_per_step": unknowns, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms / args.steps, "setup_s": setup_s, "iterations": hist,
+                      "max_relres": max(rrs), "levels": {str(L): levels.count(L) for L in sorted(set(levels))},
+                      "config": "levels U{6..10}, log10 alpha ~ U[-8,0], y_D ~ U(-1,1), seed 2; "
+                                f"{args.smoother.upper()} {args.cycle}(2,2), FP32 cycles in FP64 refinement"}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.protocol:
+    if args.batch:
+        if rank == 0:
+            run_batch(args)
+    elif args.protocol:
         if rank == 0:
             run_protocol(args)
     elif args.impl == "reference":

@@ -420,8 +420,8 @@ int default_cluster(int n, bool fp32) {
 
 // Dense map of the gamma coarse-grid steps on level ld (from a zero initial
 // guess, the steps are linear in the right-hand side): computed column by column
-// in FP64 by the single-block kernel, one block per unit vector, with the
-// operator scaled as the cycles use it; stored in the cycles' precision.
+// by the single-block kernel, one block per unit vector, in the cycles'
+// precision and with the operator scaled as the cycles use it.
 int build_dense_coarse(mg_ctx* H, double km) {
     int ld = H->ld;
     int64_t m = 2 * (int64_t)((1 << ld) + 1) * ((1 << ld) + 1);
@@ -433,8 +433,11 @@ int build_dense_coarse(mg_ctx* H, double km) {
     double inv[18 * 18];
     coarse_inverse(H->alpha, H->fp32, km, inv);
     CK(cudaMemcpy(ainv64, inv, sizeof(inv), cudaMemcpyHostToDevice));
-    CtaParams<double> C = make_cta<double>(H, ld, H->fp32, km);
-    cudaError_t e = launch_coarse_basis<double>(C, ainv64, H->o.cycle, tmp, 0);
+    // the columns in the precision of the cycles they replace (FP32 cycles run
+    // about 64x faster than FP64 on GB300; the coarsest solve stays FP64)
+    cudaError_t e = H->fp32 ? launch_coarse_basis<float>(make_cta<float>(H, ld, true, km), ainv64, H->o.cycle, tmp, 0)
+                            : launch_coarse_basis<double>(make_cta<double>(H, ld, false, km), ainv64, H->o.cycle,
+                                                          tmp, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     int rc = AAOMG_OK;
     if (e != cudaSuccess) rc = fail(AAOMG_ERR_CUDA, std::string("dense coarse map: ") + cudaGetErrorString(e));

@@ -264,6 +264,7 @@ cudaError_t launch_coarse_basis(const CtaParams<T>& C, const double* ainv, int n
     return cudaGetLastError();
 }
 
+template cudaError_t launch_coarse_basis<float>(const CtaParams<float>&, const double*, int, double*, cudaStream_t);
 template cudaError_t launch_coarse_basis<double>(const CtaParams<double>&, const double*, int, double*, cudaStream_t);
 template size_t coarse_smem_bytes<float>(int);
 template size_t coarse_smem_bytes<double>(int);
