@@ -26,7 +26,10 @@
 // Storage.  The two fields of a node sit side by side (float2 / double2) in
 // power-of-two row rings, so one shared-memory access moves both fields and a
 // ring slot is a mask.  Nodes whose whole neighbourhood is interior to the grid
-// and to the window take a branch-free path with the constant interior stencil.
+// and to the window take a branch-free path with the constant interior stencil;
+// a warp holding a column within two of the left or right boundary takes the
+// same path with its columns' stencils from a small table instead (otherwise
+// that one warp would run two paths per step and hold up its whole block).
 #include <cuda_runtime.h>
 
 #include "band.h"
@@ -55,12 +58,46 @@ struct V2<double> {
     using type = double2;
 };
 
+// Stencils of a node in a row with 2 <= j <= n-2, by the class cls5(i) of its
+// column (0, 1, interior, n-1, n): mass and bare stiffness weights (0 for a
+// neighbour outside the grid), L_y^-1 of the node, N_ii^-1 of both fields, and
+// the scatter weights of both fields' updates (the column of A scaled by the
+// neighbours' L^-1, as in the interior constants sc of LevelP).
+template <typename T>
+struct ColClass {
+    T m[7], kd[7], il0, iny, inl;
+    T sc[2][7][2];
+};
+
 template <typename T, int WT>
 struct BandSmem {
     typename V2<T>::type X[kRing][WT];
     typename V2<T>::type R[kRRing][WT];
     typename V2<T>::type F[kFRing][WT];
+    ColClass<T> cls[5];
 };
+
+template <typename T>
+__device__ void col_class_init(const LevelP<T>& P, int k, ColClass<T>& C) {
+    const int n = P.n;
+    const int i = k <= 2 ? k : n - 4 + k, j = 2;  // representative node of the class
+    double m[7], kd[7];
+    row_coeffs_general<double>(i, j, n, (double)P.h2, m, kd);
+    C.il0 = inv_ly(P, i, j);
+    C.iny = inv_n(P, 0, i, j);
+    C.inl = inv_n(P, 1, i, j);
+    for (int o = 0; o < 7; ++o) {
+        const int ii = i + DI(o), jj = j + DJ(o);
+        const double il = in_grid(ii, jj, n) ? (double)inv_ly(P, ii, jj) : 0.0;
+        const double ko = (double)P.c * (kd[o] + (double)P.km * m[o]);
+        C.m[o] = (T)m[o];
+        C.kd[o] = (T)kd[o];
+        C.sc[0][o][0] = (T)(m[o] * il);  // y update: rh_y -= m p/L, rh_l -= cK p/L_l
+        C.sc[0][o][1] = (T)(ko * il * (double)P.invd);
+        C.sc[1][o][0] = (T)(ko * il);  // lambda update: rh_y -= cK p/L, rh_l += m p/L
+        C.sc[1][o][1] = (T)(-m[o] * il);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
@@ -159,6 +196,76 @@ __device__ __forceinline__ void band_update_fast(const LevelP<T>& P, BandSmem<T,
     rows_lsgs_fast<T>(P, field, S->X[sx], S->R[s], S->R[sp], S->R[sm], t);
 }
 
+// ---------------------------------------------- boundary-column path ----
+// The rows 2..n-2 of a column near the left or right boundary: the stencils of
+// the column's class from the table, neighbours outside the grid weighted 0
+// (their ring slots hold zeros).  A warp that holds such a column runs this
+// path on all its lanes, so it never executes two paths per step.
+template <typename T, typename V2>
+__device__ __forceinline__ void class_dots(const ColClass<T>& C, const V2 (&nb)[7], V2& M, V2& K) {
+    M = pmul(psplat(C.m[0]), nb[0]);
+    K = pmul(psplat(C.kd[0]), nb[0]);
+#pragma unroll
+    for (int o = 1; o < 7; ++o) {
+        M = pfma(psplat(C.m[o]), nb[o], M);
+        K = pfma(psplat(C.kd[o]), nb[o], K);
+    }
+}
+
+template <typename V2>
+__device__ __forceinline__ void ring_load7(const V2* rs, const V2* rsp, const V2* rsm, int t, V2 (&nb)[7]) {
+    nb[0] = rs[t];
+    nb[1] = rs[t + 1];
+    nb[2] = rs[t - 1];
+    nb[3] = rsp[t];
+    nb[4] = rsm[t];
+    nb[5] = rsp[t + 1];
+    nb[6] = rsm[t - 1];
+}
+
+template <typename T, int WT>
+__device__ __forceinline__ void band_resid_col(const LevelP<T>& P, const ColClass<T>& C, BandSmem<T, WT>* S, int t,
+                                               int sxm, int sx, int sxp, int sr, int sf) {
+    using V2 = typename V2<T>::type;
+    V2 nb[7], M, K;
+    ring_load7(S->X[sx], S->X[sxp], S->X[sxm], t, nb);
+    class_dots(C, nb, M, K);
+    T ay, al;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, ay, al);
+    const V2 fv = S->F[sf][t];
+    const T il = C.il0;
+    S->R[sr][t] = pmake<T>((fv.x - ay) * il, (fv.y - al) * (il * P.invd));
+}
+
+template <typename T, int WT>
+__device__ __forceinline__ void band_update_col(const LevelP<T>& P, const ColClass<T>& C, BandSmem<T, WT>* S,
+                                                int field, int t, int sm, int s, int sp, int sx) {
+    using V2 = typename V2<T>::type;
+    V2 sc[7];  // read before the first store
+#pragma unroll
+    for (int o = 0; o < 7; ++o) sc[o] = pmake<T>(C.sc[field][o][0], C.sc[field][o][1]);
+    const T inv_nd = field == 0 ? C.iny : C.inl;
+    V2* rs = S->R[s];
+    V2* rsp = S->R[sp];
+    V2* rsm = S->R[sm];
+    V2 nb[7], M, K;
+    ring_load7(rs, rsp, rsm, t, nb);
+    class_dots(C, nb, M, K);
+    T qy, ql;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T pv = (field == 0 ? qy : ql) * inv_nd;
+    if (field == 0) S->X[sx][t].x += pv;
+    else S->X[sx][t].y += pv;
+    const V2 mp = psplat(-pv);
+    rs[t] = pfma(mp, sc[0], nb[0]);
+    rs[t + 1] = pfma(mp, sc[1], nb[1]);
+    rs[t - 1] = pfma(mp, sc[2], nb[2]);
+    rsp[t] = pfma(mp, sc[3], nb[3]);
+    rsm[t] = pfma(mp, sc[4], nb[4]);
+    rsp[t + 1] = pfma(mp, sc[5], nb[5]);
+    rsm[t - 1] = pfma(mp, sc[6], nb[6]);
+}
+
 template <typename T, int WT>
 __global__ void __launch_bounds__(2 * WT) k_lsgs_band(LevelP<T> P, const T* __restrict__ f,
                                                       const T* __restrict__ xin, T* __restrict__ xout, int W, int Hs) {
@@ -185,8 +292,13 @@ __global__ void __launch_bounds__(2 * WT) k_lsgs_band(LevelP<T> P, const T* __re
     // this column (and its neighbours) interior to the grid and the window
     const bool col_fast = c >= 2 && c <= P.n - 2;
     const int jfl = max(2, jl + 1), jfh = min(P.n - 2, jh - 1);  // rows whose neighbourhood is fast
+    // a warp with a working column near the left or right boundary takes the
+    // table path on all its lanes (rows jfl..jfh)
+    const bool warp_fast = !__any_sync(0xffffffffu, col_work && !col_fast);
+    const ColClass<T>& C = S->cls[cls5(min(max(c, 0), P.n), P.n)];
 
     using V2T = typename V2<T>::type;
+    if (threadIdx.x < 5) col_class_init<T>(P, threadIdx.x, S->cls[threadIdx.x]);
     if (half == 0) {
         for (int r = 0; r < kRing; ++r) S->X[r][tid] = V2T{T(0), T(0)};
     } else {
@@ -224,28 +336,40 @@ __global__ void __launch_bounds__(2 * WT) k_lsgs_band(LevelP<T> P, const T* __re
         if (half == 0) {
             issue(tau + kPre);
             if (col_work && jy >= jl && jy <= jh) {
-                if (col_fast && jy >= jfl && jy <= jfh)
-                    band_update_fast<T, WT>(P, S, 0, tid, (jy - 1) & (kRRing - 1), jy & (kRRing - 1),
-                                            (jy + 1) & (kRRing - 1), jy & (kRing - 1));
-                else
+                if (jy >= jfl && jy <= jfh) {
+                    if (warp_fast)
+                        band_update_fast<T, WT>(P, S, 0, tid, (jy - 1) & (kRRing - 1), jy & (kRRing - 1),
+                                                (jy + 1) & (kRRing - 1), jy & (kRing - 1));
+                    else
+                        band_update_col<T, WT>(P, C, S, 0, tid, (jy - 1) & (kRRing - 1), jy & (kRRing - 1),
+                                               (jy + 1) & (kRRing - 1), jy & (kRing - 1));
+                } else
                     band_update_general<T, WT>(P, V, 0, c, jy);
             }
         } else if (col_work) {
             // rh of row rho = tau - 2 from the original iterate
             const int rho = tau - 2;
             if (rho >= jl && rho <= jh) {
-                if (col_fast && rho >= jfl && rho <= jfh)
-                    band_resid_fast<T, WT>(P, S, tid, (rho - 1) & (kRing - 1), rho & (kRing - 1),
-                                           (rho + 1) & (kRing - 1), rho & (kRRing - 1), rho & (kFRing - 1));
-                else
+                if (rho >= jfl && rho <= jfh) {
+                    if (warp_fast)
+                        band_resid_fast<T, WT>(P, S, tid, (rho - 1) & (kRing - 1), rho & (kRing - 1),
+                                               (rho + 1) & (kRing - 1), rho & (kRRing - 1), rho & (kFRing - 1));
+                    else
+                        band_resid_col<T, WT>(P, C, S, tid, (rho - 1) & (kRing - 1), rho & (kRing - 1),
+                                              (rho + 1) & (kRing - 1), rho & (kRRing - 1), rho & (kFRing - 1));
+                } else
                     band_resid_general<T, WT>(P, V, c, rho);
             }
             // the lambda phase that meets this column at this step
             if (jlam >= jl && jlam <= jh) {
-                if (col_fast && jlam >= jfl && jlam <= jfh)
-                    band_update_fast<T, WT>(P, S, 1, tid, (jlam - 1) & (kRRing - 1), jlam & (kRRing - 1),
-                                            (jlam + 1) & (kRRing - 1), jlam & (kRing - 1));
-                else
+                if (jlam >= jfl && jlam <= jfh) {
+                    if (warp_fast)
+                        band_update_fast<T, WT>(P, S, 1, tid, (jlam - 1) & (kRRing - 1), jlam & (kRRing - 1),
+                                                (jlam + 1) & (kRRing - 1), jlam & (kRing - 1));
+                    else
+                        band_update_col<T, WT>(P, C, S, 1, tid, (jlam - 1) & (kRRing - 1), jlam & (kRRing - 1),
+                                               (jlam + 1) & (kRRing - 1), jlam & (kRing - 1));
+                } else
                     band_update_general<T, WT>(P, V, 1, c, jlam);
             }
             const int ro = tau - kLag;
