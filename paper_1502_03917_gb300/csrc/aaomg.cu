@@ -44,6 +44,7 @@ struct Lev {
     void* rh = nullptr;
     BandGrid bg{};
     int cs = 0;              // smoothing calls in one launch: of one block (1) or a cluster of cs blocks; 0: no
+    void* ctab = nullptr;    // its boundary-class table (EdgeClass[25] in the cycles' precision)
     LevelP<float> pf{};
     LevelP<double> pd{};
 };
@@ -290,7 +291,7 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     if (v.cs > 0) {
         // the whole smoothing call in one launch of one block or one cluster
         // (x and rh, or for CGS x and f, in shared memory)
-        launch_smooth_strips<T>(P, H->o.smoother, steps, x, f, v.cs, s);
+        launch_smooth_strips<T>(P, (const EdgeClass<T>*)v.ctab, H->o.smoother, steps, x, f, v.cs, s);
         H->rec_kernels += 1;
         return;
     }
@@ -406,6 +407,40 @@ int record_iteration(mg_ctx* H, cudaStream_t s) {
         launch_refine_update(H->fine64, H->x64, (const float*)v.x, v.ld, v.fs, s);
         H->rec_kernels += 1;
     }
+    return AAOMG_OK;
+}
+
+// The 25 boundary classes of level v for the one-launch smoothing kernel
+// (EdgeClass, strips.h), from the FP64 coefficients, in the cycles' precision.
+template <typename T>
+int build_class_table(mg_ctx* H, Lev& v, double km) {
+    const int n = v.n;
+    const Coef K = make_coef(n, H->alpha, H->fp32, km);
+    EdgeClass<T> tab[25];
+    auto rep = [n](int a) { return a <= 2 ? a : n - 4 + a; };  // nodes 0, 1, 2, n-1, n
+    for (int k = 0; k < 25; ++k) {
+        const int i = rep(k % 5), j = rep(k / 5);
+        double m[7], kd[7];
+        row_coeffs_general<double>(i, j, n, K.h2, m, kd);
+        EdgeClass<T>& C = tab[k];
+        for (int o = 0; o < 7; ++o) {
+            const int ii = i + DI(o), jj = j + DJ(o);
+            const double il = in_grid(ii, jj, n) ? 1.0 / coef_ly(K, ii, jj) : 0.0;
+            const double ko = K.c * (kd[o] + km * m[o]);
+            C.m[o] = (T)m[o];
+            C.kd[o] = (T)kd[o];
+            C.il[o] = (T)il;
+            C.sc[0][o][0] = (T)(m[o] * il);  // y update: rh_y -= m p/L, rh_l -= cK p/L_l
+            C.sc[0][o][1] = (T)(ko * il / K.d);
+            C.sc[1][o][0] = (T)(ko * il);  // lambda update: rh_y -= cK p/L, rh_l += m p/L
+            C.sc[1][o][1] = (T)(-m[o] * il);
+        }
+        C.iny = (T)(1.0 / coef_nd(K, i, j, 0));
+        C.inl = (T)(1.0 / coef_nd(K, i, j, 1));
+    }
+    int rc = dalloc(H, &v.ctab, sizeof(tab));
+    if (rc) return rc;
+    CK(cudaMemcpy(v.ctab, tab, sizeof(tab), cudaMemcpyHostToDevice));
     return AAOMG_OK;
 }
 
@@ -737,6 +772,8 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
                 if (runs(cs)) v.cs = cs;
             if (!v.cs && runs(1)) v.cs = 1;
         }
+        if (!rc && v.cs > 0)
+            rc = H->fp32 ? build_class_table<float>(H, v, km) : build_class_table<double>(H, v, km);
     }
     if (rc) {
         mg_destroy(H);

@@ -64,31 +64,11 @@ struct Strip {
 // ------------------------------------------------------- edge nodes --
 // Nodes within two rows or columns of the boundary.  Their stencils, the L_y^-1
 // of their neighbours and their N_ii^-1 depend only on the node's boundary
-// class cls5(i) + 5 cls5(j); each block tabulates the 25 classes in shared
-// memory at the start (no global-memory latency inside a phase).  An LSGS
+// class cls5(i) + 5 cls5(j); each block copies the level's 25-class table
+// (EdgeClass, built on the host) into shared memory at the start, so a phase
+// sees no global-memory latency.  An LSGS
 // update reads the table entries its scatter needs before its first store, so
 // that no table load waits behind a store it might alias.
-template <typename T>
-struct EdgeClass {
-    T m[7], kd[7], il[7];  // il: L_y^-1 of neighbour o (0 outside the grid)
-    T iny, inl;            // N_ii^-1 of the two fields
-};
-
-template <typename T, int N>
-__device__ void edge_class_init(const LevelP<T>& P, int k, EdgeClass<T>& C) {
-    // a representative node of each class: 0, 1, 2, N-1, N
-    auto rep = [](int a) { return a <= 2 ? a : N - 4 + a; };
-    const int i = rep(k % 5), j = rep(k / 5);
-    row_coeffs_general<T>(i, j, N, P.h2, C.m, C.kd);
-#pragma unroll
-    for (int o = 0; o < 7; ++o) {
-        const int ii = i + DI(o), jj = j + DJ(o);
-        C.il[o] = in_grid(ii, jj, N) ? inv_ly(P, ii, jj) : T(0);
-    }
-    C.iny = inv_n(P, 0, i, j);
-    C.inl = inv_n(P, 1, i, j);
-}
-
 template <typename T, int N, typename RowPtr, typename V2>
 __device__ __forceinline__ void cl_gather(const RowPtr (&rows)[3], int i, int j, const EdgeClass<T>& C, V2 (&v)[7],
                                           T& My, T& Ky, T& Ml, T& Kl) {
@@ -138,9 +118,9 @@ template <typename T, int N, class S_>
 __device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass<T>& C, int field, const S_& S,
                                              int i, int j) {
     using V2 = typename P2<T>::t;
-    T il[7];  // read before the first store
+    V2 sc[7];  // read before the first store
 #pragma unroll
-    for (int o = 0; o < 7; ++o) il[o] = C.il[o];
+    for (int o = 0; o < 7; ++o) sc[o] = pmake<T>(C.sc[field][o][0], C.sc[field][o][1]);
     const T inv_nd = field == 0 ? C.iny : C.inl;
     V2* const rows[3] = {S.rrow(j - 1), S.rrow(j), S.rrow(j + 1)};
     V2 v[7];
@@ -151,16 +131,11 @@ __device__ __forceinline__ void cl_lsgs_edge(const LevelP<T>& P, const EdgeClass
     V2* xr = S.xrow(j);
     if (field == 0) xr[i].x += p;
     else xr[i].y += p;
-    // column of A for this unknown: field y -> (m, cK); field lambda -> (cK, -dm)
+    const V2 mp = psplat(-p);
 #pragma unroll
     for (int o = 0; o < 7; ++o) {
         const int ii = i + DI(o), jj = j + DJ(o);
-        if (!in_grid(ii, jj, N)) continue;
-        const T mp = C.m[o] * p;
-        const T kp = P.c * (C.kd[o] * p + P.km * mp);
-        V2* q = rows[DJ(o) + 1] + ii;
-        if (field == 0) *q = pmake<T>(v[o].x - mp * il[o], v[o].y - kp * (il[o] * P.invd));
-        else *q = pmake<T>(v[o].x - kp * il[o], v[o].y + mp * il[o]);
+        if (in_grid(ii, jj, N)) rows[DJ(o) + 1][ii] = pfma(mp, sc[o], v[o]);
     }
 }
 
@@ -178,22 +153,25 @@ struct StripEdges {
     __device__ __forceinline__ int per_col(int c) const { return c < 0 ? nrows : (nrows + K - 1) / K; }
     __device__ __forceinline__ int count(int c) const { return nfull * (c < 0 ? N + 1 : FPR) + 4 * per_col(c); }
     __device__ __forceinline__ bool node(int t, int c, int& i, int& j) const {
-        const int per = c < 0 ? N + 1 : FPR;
-        if (t < nfull * per) {
-            const int r = t / per, k = t - r * per;
+        return c < 0 ? node_any<N + 1, true>(t, c, i, j) : node_any<FPR, false>(t, c, i, j);
+    }
+    template <int PER, bool ALL>
+    __device__ __forceinline__ bool node_any(int t, int c, int& i, int& j) const {
+        if (t < nfull * PER) {
+            const int r = t / PER, k = t - r * PER;
             j = r < first_full_hi ? r : N - 1 + (r - first_full_hi);
-            i = c < 0 ? k : ((c - A * j) % K + K) % K + K * k;
+            i = ALL ? k : ((c - A * j) % K + K) % K + K * k;
             return i <= N;
         }
-        t -= nfull * per;
-        const int pc = per_col(c);
+        t -= nfull * PER;
+        const int pc = ALL ? nrows : (nrows + K - 1) / K;
         int q = 0, k = t;
         while (k >= pc && q < 3) {  // q = t / pc for t < 4 pc
             k -= pc;
             ++q;
         }
         i = q < 2 ? q : N - 3 + q;
-        j = c < 0 ? ja + k : ja + ((AINV * (c - i) - ja) % K + K) % K + K * k;
+        j = ALL ? ja + k : ja + ((AINV * (c - i) - ja) % K + K) % K + K * k;
         return j < ja + nrows;
     }
 };
@@ -232,8 +210,10 @@ __device__ __forceinline__ void cl_cgs_edge(const LevelP<T>& P, const EdgeClass<
 // count) come first in every pass, then the strip's edge nodes, so that no warp
 // mixes the two paths.
 template <typename T, int N, bool CL>
-__global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> P, int smoother, int steps,
-                                                                      T* __restrict__ x, const T* __restrict__ f) {
+__global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> P,
+                                                                      const EdgeClass<T>* __restrict__ ctab,
+                                                                      int smoother, int steps, T* __restrict__ x,
+                                                                      const T* __restrict__ f) {
     using V2 = typename P2<T>::t;
     constexpr int LD = N + 1;
     constexpr int W = N - 3;             // deep-interior columns
@@ -276,7 +256,12 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
     };
 
     const int g = threadIdx.x, G = blockDim.x;
-    if (g < 25) edge_class_init<T, N>(P, g, s_cls[g]);
+    {
+        constexpr int words = 25 * sizeof(EdgeClass<T>) / sizeof(T);
+        T* dst = reinterpret_cast<T*>(s_cls);
+        const T* src = reinterpret_cast<const T*>(ctab);
+        for (int t = g; t < words; t += G) dst[t] = src[t];
+    }
     const int nown = (S.r1 - S.r0) * LD;
     const int64_t base = (int64_t)S.r0 * LD;
     for (int t = g; t < nown; t += G) X[t] = pmake<T>(x[base + t], x[base + t + P.fs]);
@@ -473,15 +458,15 @@ int strips_max_active(int n, int cs) {
 }
 
 template <typename T>
-cudaError_t launch_smooth_strips(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, int cs,
-                                 cudaStream_t s) {
+cudaError_t launch_smooth_strips(const LevelP<T>& P, const EdgeClass<T>* ctab, int smoother, int steps, T* x,
+                                 const T* f, int cs, cudaStream_t s) {
     cudaLaunchAttribute at[1];
     if (cs == 1) {
         switch (P.n) {
 #define B_(N)                                                                                        \
     case N: {                                                                                        \
         cudaLaunchConfig_t cfg = strips_config<T, N, false>(1, s, at);                               \
-        return cudaLaunchKernelEx(&cfg, k_smooth_strips<T, N, false>, P, smoother, steps, x, f);     \
+        return cudaLaunchKernelEx(&cfg, k_smooth_strips<T, N, false>, P, ctab, smoother, steps, x, f);     \
     }
             AAOMG_BLOCK_N(B_)
 #undef B_
@@ -492,7 +477,7 @@ cudaError_t launch_smooth_strips(const LevelP<T>& P, int smoother, int steps, T*
 #define C_(N)                                                                                       \
     case N: {                                                                                       \
         cudaLaunchConfig_t cfg = strips_config<T, N, true>(cs, s, at);                              \
-        return cudaLaunchKernelEx(&cfg, k_smooth_strips<T, N, true>, P, smoother, steps, x, f);     \
+        return cudaLaunchKernelEx(&cfg, k_smooth_strips<T, N, true>, P, ctab, smoother, steps, x, f);     \
     }
         AAOMG_CLUSTER_N(C_)
 #undef C_
@@ -505,7 +490,8 @@ cudaError_t launch_smooth_strips(const LevelP<T>& P, int smoother, int steps, T*
     template cudaError_t strips_prepare<T>();                                                                   \
     template bool strips_fit<T>(int, int);                                                                      \
     template int strips_max_active<T>(int, int);                                                                \
-    template cudaError_t launch_smooth_strips<T>(const LevelP<T>&, int, int, T*, const T*, int, cudaStream_t);
+    template cudaError_t launch_smooth_strips<T>(const LevelP<T>&, const EdgeClass<T>*, int, int, T*, const T*, int, \
+                                                 cudaStream_t);
 AAOMG_STRIPS_INST(float)
 AAOMG_STRIPS_INST(double)
 

@@ -14,7 +14,7 @@ constexpr int strip_threads() {
     return sizeof(T) == 4 ? 1024 : 512;
 }
 // dynamic shared memory per block: 227 KB less room for a small static table
-constexpr int kStripSmemMax = 227 * 1024 - 8 * 1024;
+constexpr int kStripSmemMax = 227 * 1024 - 12 * 1024;
 constexpr int kClusterMax = 16;  // blocks per cluster; above 8 needs the non-portable size
 
 // level sizes (cells per side) with a single-block kernel and with a cluster kernel
@@ -24,6 +24,18 @@ constexpr bool cluster_level(int n) { return n == 64 || n == 128 || n == 256; }
 // rows [row_lo(k), row_lo(k+1)) of a level with `rows` grid rows belong to
 // block k of cs blocks
 AAOMG_HD int strip_row_lo(int k, int rows, int cs) { return (int)(((long long)k * rows) / cs); }
+
+// Coefficients of the nodes of one boundary class cls5(i) + 5 cls5(j) (25
+// classes per level; class 12 is the deep interior): mass and bare stiffness
+// weights of the 7 offsets, L_y^-1 of each neighbour (0 outside the grid),
+// N_ii^-1 of both fields, and the LSGS scatter weights of both fields (the
+// column of A scaled by the neighbours' L^-1).  Built on the host in FP64.
+template <typename T>
+struct EdgeClass {
+    T m[7], kd[7], il[7];
+    T iny, inl;
+    T sc[2][7][2];
+};
 
 // shared memory per block: x and rh pairs of the largest strip
 template <typename T>
@@ -40,7 +52,7 @@ int strips_max_active(int n, int cs);
 // `steps` smoothing steps (smoother 0 NE, 1 LSGS, 2 sLSGS) on one level in one
 // launch of cs blocks (cs = 1: a single block; else one cluster)
 template <typename T>
-cudaError_t launch_smooth_strips(const LevelP<T>& P, int smoother, int steps, T* x, const T* f, int cs,
-                                 cudaStream_t s);
+cudaError_t launch_smooth_strips(const LevelP<T>& P, const EdgeClass<T>* ctab, int smoother, int steps, T* x,
+                                 const T* f, int cs, cudaStream_t s);
 
 }  // namespace aaomg
