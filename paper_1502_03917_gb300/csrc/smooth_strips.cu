@@ -85,17 +85,16 @@ __device__ __forceinline__ void cl_gather(const RowPtr (&rows)[3], int i, int j,
 }
 
 template <typename T, int N, class S_>
-__device__ __forceinline__ void cl_resid_edge(const LevelP<T>& P, const EdgeClass<T>& C, const T* f, const S_& S,
-                                              int i, int j) {
+__device__ __forceinline__ void cl_resid_edge(const LevelP<T>& P, const EdgeClass<T>& C,
+                                              typename P2<T>::t fv, const S_& S, int i, int j) {
     using V2 = typename P2<T>::t;
     const V2* const rows[3] = {S.xrow(j - 1), S.xrow(j), S.xrow(j + 1)};
     V2 v[7];
     T My, Ky, Ml, Kl, ay, al;
     cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
     rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
-    const int64_t p = (int64_t)j * (N + 1) + i;
     const T il = C.il[0];
-    S.rrow(j)[i] = pmake<T>((f[p] - ay) * il, (f[p + P.fs] - al) * (il * P.invd));
+    S.rrow(j)[i] = pmake<T>((fv.x - ay) * il, (fv.y - al) * (il * P.invd));
 }
 
 template <typename T, int N, class S_>
@@ -264,7 +263,12 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
     }
     const int nown = (S.r1 - S.r0) * LD;
     const int64_t base = (int64_t)S.r0 * LD;
-    for (int t = g; t < nown; t += G) X[t] = pmake<T>(x[base + t], x[base + t + P.fs]);
+    // x, and for LSGS, sLSGS and CGS also f into R (one global round trip;
+    // the residual then overwrites each node's f in place)
+    for (int t = g; t < nown; t += G) {
+        X[t] = pmake<T>(x[base + t], x[base + t + P.fs]);
+        if (smoother != 0) R[t] = pmake<T>(f[base + t], f[base + t + P.fs]);
+    }
     barrier();
 
     const int ja = max(S.r0, 2), jb = min(S.r1, N - 1);
@@ -283,11 +287,16 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
                 if (t < nia) {
                     const int r = t / W, i = 2 + t - r * W, j = ja + r;
                     const int64_t p = (int64_t)j * LD + i;
-                    S.rrow(j)[i] = rows_resid_fast<T>(P, S.xrow(j), S.xrow(j + 1), S.xrow(j - 1), i, f[p], f[p + P.fs]);
+                    const V2 fv = smoother == 0 ? pmake<T>(f[p], f[p + P.fs]) : S.rrow(j)[i];
+                    S.rrow(j)[i] = rows_resid_fast<T>(P, S.xrow(j), S.xrow(j + 1), S.xrow(j - 1), i, fv.x, fv.y);
                 }
             } else {
                 int i, j;
-                if (SE.node(t - niap, -1, i, j)) cl_resid_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], f, S, i, j);
+                if (SE.node(t - niap, -1, i, j)) {
+                    const int64_t p = (int64_t)j * LD + i;
+                    const V2 fv = smoother == 0 ? pmake<T>(f[p], f[p + P.fs]) : S.rrow(j)[i];
+                    cl_resid_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], fv, S, i, j);
+                }
             }
         }
         barrier();
@@ -313,8 +322,6 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
 
     if (smoother == 3) {
         // CGS keeps no residual: R holds the strip's (f_y, f_lambda) pairs
-        for (int t = g; t < nown; t += G) R[t] = pmake<T>(f[base + t], f[base + t + P.fs]);
-        __syncthreads();
         constexpr int CPR3 = (N - 3 + 2) / 3;  // deep-interior slots per row of one colour
         StripEdges<N, 3, 1, 1> SE3;
         SE3.first_full_hi = SE.first_full_hi;
