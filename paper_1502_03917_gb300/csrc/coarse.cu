@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "coarse.h"
+#include "pdl.h"
 #include "stencil.cuh"
 
 namespace aaomg {
@@ -168,6 +169,7 @@ template <typename T>
 __global__ void __launch_bounds__(cta_threads<T>()) k_coarse_cycle(CtaParams<T> C, const T* __restrict__ fg,
                                                               T* __restrict__ xg, const double* __restrict__ ainv,
                                                               int ncycles) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem[];
     CtaState<T> S;
     double* a = reinterpret_cast<double*>(smem);
@@ -251,7 +253,7 @@ cudaError_t coarse_prepare() {
 
 template <typename T>
 void launch_coarse_cycle(const CtaParams<T>& C, const T* f, T* x, const double* ainv, int ncycles, cudaStream_t s) {
-    k_coarse_cycle<T><<<1, cta_threads<T>(), coarse_smem_bytes<T>(C.lc), s>>>(C, f, x, ainv, ncycles);
+    launch_pdl(k_coarse_cycle<T>, 1, cta_threads<T>(), coarse_smem_bytes<T>(C.lc), s, C, f, x, ainv, ncycles);
 }
 
 template <typename T>

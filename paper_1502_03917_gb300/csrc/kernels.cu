@@ -7,6 +7,7 @@
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
+#include "pdl.h"
 #include "lean.cuh"
 #include "stencil.cuh"
 
@@ -25,6 +26,7 @@ namespace {
 // constants); N = 0: any n
 template <typename T, int N>
 __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __restrict__ x, T* __restrict__ rhv) {
+    pdl_wait();
     using V2 = typename P2<T>::t;
     V2* rh = reinterpret_cast<V2*>(rhv);  // (y, lambda) pairs
     const int n = N > 0 ? N : P.n, ld = n + 1, fs = ld * ld;
@@ -45,6 +47,7 @@ __global__ void k_resid_hat(LevelP<T> P, const T* __restrict__ f, const T* __res
 // Algorithm 1 update: x += tau L^{-1} A rh (A symmetric), with rh = L^{-1} r
 template <typename T, int N>
 __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict__ rhv) {
+    pdl_wait();
     using V2 = typename P2<T>::t;
     V2* rh = reinterpret_cast<V2*>(const_cast<T*>(rhv));
     const int n = N > 0 ? N : P.n, ld = n + 1, fs = ld * ld;
@@ -68,6 +71,7 @@ __global__ void k_ne_update(LevelP<T> P, T* __restrict__ x, const T* __restrict_
 // neighbour, so the updates of a phase are independent and race-free.
 template <typename T, int N>
 __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__ x, T* __restrict__ rhv) {
+    pdl_wait();
     using V2 = typename P2<T>::t;
     V2* rh = reinterpret_cast<V2*>(rhv);
     const int n = N > 0 ? N : P.n, ld = n + 1, fs = ld * ld;
@@ -88,6 +92,7 @@ __global__ void k_lsgs_phase(LevelP<T> P, int field, int colour, T* __restrict__
 // colour in that row.
 template <typename T>
 __global__ void k_cgs_phase(LevelP<T> P, int colour, const T* __restrict__ f, T* __restrict__ x) {
+    pdl_wait();
     const int spr = (P.n + 1 + 2) / 3;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (P.n + 1) * spr) return;
@@ -102,6 +107,7 @@ __global__ void k_cgs_phase(LevelP<T> P, int colour, const T* __restrict__ f, T*
 template <typename T>
 __global__ void k_restrict(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ f, const T* __restrict__ x,
                            T* __restrict__ fc, T* __restrict__ xc) {
+    pdl_wait();
     int I = blockIdx.x * blockDim.x + threadIdx.x;
     int J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I > Pc.n || J > Pc.n) return;
@@ -117,6 +123,7 @@ __global__ void k_restrict(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ f, 
 // x += P xc: nodal interpolation of the coarse P1 function at the fine node
 template <typename T>
 __global__ void k_prolong(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ xc, T* __restrict__ x) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > Pf.n || j > Pf.n) return;
@@ -130,6 +137,7 @@ __global__ void k_prolong(LevelP<T> Pf, LevelP<T> Pc, const T* __restrict__ xc, 
 // exact solve on the coarsest grid (18 unknowns): x = A_1^{-1} f in FP64
 template <typename T>
 __global__ void k_coarsest(const double* __restrict__ ainv, const T* __restrict__ f, T* __restrict__ x, int64_t fs) {
+    pdl_wait();
     __shared__ double fb[18];
     int t = threadIdx.x;
     if (t < 18) fb[t] = (double)f[(t < 9 ? t : fs + t - 9)];
@@ -315,40 +323,40 @@ inline int split_threads(int n, bool colour) {
 template <typename T>
 void launch_resid_hat(const LevelP<T>& P, const T* f, const T* x, T* rh, cudaStream_t s) {
     int nb = (split_threads(P.n, false) + 255) / 256;
-#define L_(N) k_resid_hat<T, N><<<nb, 256, 0, s>>>(P, f, x, rh)
+#define L_(N) launch_pdl(k_resid_hat<T, N>, nb, 256, 0, s, P, f, x, rh)
     AAOMG_BY_N(P.n, L_)
 #undef L_
 }
 template <typename T>
 void launch_ne_update(const LevelP<T>& P, T* x, const T* rh, cudaStream_t s) {
     int nb = (split_threads(P.n, false) + 255) / 256;
-#define L_(N) k_ne_update<T, N><<<nb, 256, 0, s>>>(P, x, rh)
+#define L_(N) launch_pdl(k_ne_update<T, N>, nb, 256, 0, s, P, x, rh)
     AAOMG_BY_N(P.n, L_)
 #undef L_
 }
 template <typename T>
 void launch_lsgs_phase(const LevelP<T>& P, int field, int colour, T* x, T* rh, cudaStream_t s) {
     int nb = (split_threads(P.n, true) + 255) / 256;
-#define L_(N) k_lsgs_phase<T, N><<<nb, 256, 0, s>>>(P, field, colour, x, rh)
+#define L_(N) launch_pdl(k_lsgs_phase<T, N>, nb, 256, 0, s, P, field, colour, x, rh)
     AAOMG_BY_N(P.n, L_)
 #undef L_
 }
 template <typename T>
 void launch_cgs_phase(const LevelP<T>& P, int colour, const T* f, T* x, cudaStream_t s) {
     const int slots = (P.n + 1) * ((P.n + 1 + 2) / 3);
-    k_cgs_phase<T><<<(slots + 255) / 256, 256, 0, s>>>(P, colour, f, x);
+    launch_pdl(k_cgs_phase<T>, (slots + 255) / 256, 256, 0, s, P, colour, f, x);
 }
 template <typename T>
 void launch_restrict(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* f, const T* x, T* fc, T* xc, cudaStream_t s) {
-    k_restrict<T><<<grid2(Pc.n + 1, Pc.n + 1, kBlk2), kBlk2, 0, s>>>(Pf, Pc, f, x, fc, xc);
+    launch_pdl(k_restrict<T>, grid2(Pc.n + 1, Pc.n + 1, kBlk2), kBlk2, 0, s, Pf, Pc, f, x, fc, xc);
 }
 template <typename T>
 void launch_prolong(const LevelP<T>& Pf, const LevelP<T>& Pc, const T* xc, T* x, cudaStream_t s) {
-    k_prolong<T><<<grid2(Pf.n + 1, Pf.n + 1, kBlk2), kBlk2, 0, s>>>(Pf, Pc, xc, x);
+    launch_pdl(k_prolong<T>, grid2(Pf.n + 1, Pf.n + 1, kBlk2), kBlk2, 0, s, Pf, Pc, xc, x);
 }
 template <typename T>
 void launch_coarsest(const double* ainv, const T* f, T* x, int64_t fs, cudaStream_t s) {
-    k_coarsest<T><<<1, 32, 0, s>>>(ainv, f, x, fs);
+    launch_pdl(k_coarsest<T>, 1, 32, 0, s, ainv, f, x, fs);
 }
 
 void launch_resid64(const LevelP<double>& P, const double* f, const double* x, double* r, float* fin, int64_t fin_ld,
@@ -399,6 +407,7 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_apply(const T* __restrict__ B, int m, const T* __restrict__ f,
                                                      T* __restrict__ x) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* fs = reinterpret_cast<T*>(smem_raw);
     for (int t = threadIdx.x; t < m; t += blockDim.x) fs[t] = f[t];
@@ -423,7 +432,7 @@ __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b
 
 template <typename T>
 void launch_dense_apply(const T* B, int m, const T* f, T* x, cudaStream_t s) {
-    k_dense_apply<T><<<(m + 7) / 8, 256, m * sizeof(T), s>>>(B, m, f, x);
+    launch_pdl(k_dense_apply<T>, (m + 7) / 8, 256, m * sizeof(T), s, B, m, f, x);
 }
 void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
     k_f64_to_f32<<<1024, 256, 0, s>>>(a, b, n);

@@ -34,6 +34,7 @@
 
 #include "band.h"
 #include "lean.cuh"
+#include "pdl.h"
 #include "pair.cuh"
 #include "stencil.cuh"
 
@@ -269,6 +270,7 @@ __device__ __forceinline__ void band_update_col(const LevelP<T>& P, const ColCla
 template <typename T, int WT>
 __global__ void __launch_bounds__(2 * WT) k_lsgs_band(LevelP<T> P, const T* __restrict__ f,
                                                       const T* __restrict__ xin, T* __restrict__ xout, int W, int Hs) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BandSmem<T, WT>* S = reinterpret_cast<BandSmem<T, WT>*>(smem_raw);
     // two threads per column: half 0 prefetches and does the y update, half 1
@@ -403,7 +405,7 @@ cudaError_t band_prepare() {
 template <typename T>
 void launch_lsgs_band(const LevelP<T>& P, const T* f, const T* xin, T* xout, const BandGrid& g, cudaStream_t s) {
     constexpr int WT = band_threads<T>();
-    k_lsgs_band<T, WT><<<dim3(g.nb, g.ns), 2 * WT, band_smem_bytes<T>(), s>>>(P, f, xin, xout, g.W, g.Hs);
+    launch_pdl(k_lsgs_band<T, WT>, dim3(g.nb, g.ns), 2 * WT, band_smem_bytes<T>(), s, P, f, xin, xout, g.W, g.Hs);
 }
 
 template size_t band_smem_bytes<float>();

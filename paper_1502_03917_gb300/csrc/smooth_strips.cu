@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "lean.cuh"
+#include "pdl.h"
 #include "stencil.cuh"
 #include "strips.h"
 
@@ -213,6 +214,7 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
                                                                       const EdgeClass<T>* __restrict__ ctab,
                                                                       int smoother, int steps, T* __restrict__ x,
                                                                       const T* __restrict__ f) {
+    pdl_wait();
     using V2 = typename P2<T>::t;
     constexpr int LD = N + 1;
     constexpr int W = N - 3;             // deep-interior columns
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
 }
 
 template <typename T, int N, bool CL>
-cudaLaunchConfig_t strips_config(int cs, cudaStream_t s, cudaLaunchAttribute* at) {
+cudaLaunchConfig_t strips_config(int cs, cudaStream_t s, cudaLaunchAttribute* at, bool pdl = true) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(strip_threads<T>(), 1, 1);
@@ -390,12 +392,17 @@ cudaLaunchConfig_t strips_config(int cs, cudaStream_t s, cudaLaunchAttribute* at
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 0;
+    if (pdl) {
+        at[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl.h
+        at[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
+        ++cfg.numAttrs;
+    }
     if (CL) {
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = cs;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.numAttrs = 1;
+        at[cfg.numAttrs].id = cudaLaunchAttributeClusterDimension;
+        at[cfg.numAttrs].val.clusterDim.x = cs;
+        at[cfg.numAttrs].val.clusterDim.y = 1;
+        at[cfg.numAttrs].val.clusterDim.z = 1;
+        ++cfg.numAttrs;
     }
     return cfg;
 }
@@ -443,13 +450,13 @@ template <typename T>
 int strips_max_active(int n, int cs) {
     if (!strips_fit<T>(n, cs)) return 0;
     if (cs == 1) return 1;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     int num = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (n) {
 #define C_(N)                                                                                  \
     case N: {                                                                                  \
-        cudaLaunchConfig_t cfg = strips_config<T, N, true>(cs, 0, at);                         \
+        cudaLaunchConfig_t cfg = strips_config<T, N, true>(cs, 0, at, false);                  \
         e = cudaOccupancyMaxActiveClusters(&num, (void*)k_smooth_strips<T, N, true>, &cfg);    \
         break;                                                                                 \
     }
@@ -467,7 +474,7 @@ int strips_max_active(int n, int cs) {
 template <typename T>
 cudaError_t launch_smooth_strips(const LevelP<T>& P, const EdgeClass<T>* ctab, int smoother, int steps, T* x,
                                  const T* f, int cs, cudaStream_t s) {
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     if (cs == 1) {
         switch (P.n) {
 #define B_(N)                                                                                        \
