@@ -101,6 +101,26 @@ def peaks():
         return None
 
 
+# ----------------------------------------------------------- multi-rank --
+def rank_max(v: float, world: int, device: str) -> float:
+    """The largest v over all ranks (the slowest replica's time); v itself for
+    one rank.  Uses the default process group (NCCL on GPUs, gloo on CPU)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all replicas processed in `steps` steps
+    divided by the slowest replica's time (ms)."""
+    return world * units_per_rank_step * steps / (ms_max / 1e3)
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) while the timed region runs."""
@@ -261,11 +281,7 @@ def run_ours(args, rank, world, local):
         return ms, its, launches, prof, clocks, xs
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(v, world, "cuda")
 
     K, W = args.steps, args.warmup
     N = ((1 << L) + 1) ** 2
@@ -274,7 +290,7 @@ def run_ours(args, rank, world, local):
     sol32 = make("fp32_refine", not args.profiling_run)
     ms, its32, launches, prof, clocks, xs32 = timed_steps(sol32, K, W)
     ms = max_over_ranks(ms)
-    value = world * unknowns_step * K / (ms / 1e3)
+    value = job_value(unknowns_step, K, world, ms)
 
     # roofline of the dominant kernel: the finest-level smoother sweeps
     pk = peaks()
