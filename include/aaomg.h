@@ -126,7 +126,8 @@ AAOMG_API int mg_rhs_from_yd(mg_handle h, const double* yD, double* f, void* str
 AAOMG_API int mg_residual(mg_handle h, const double* f, const double* x, double* r, double* relres, void* stream);
 
 /* `steps` smoothing steps of the configured smoother on the finest level:
- * x <- x + Ahat^{-1}(f - A x) (section 2; Algorithm 1 / Algorithm 2), in place
+ * x <- x + Ahat^{-1}(f - A x) (section 2; Algorithm 1, Algorithm 2, sLSGS or
+ * the CGS block step), in place
  * on x.  In FP32_REFINE mode the steps run in FP32 on x and f rounded to
  * single precision.  Device pointers, 2N doubles each. */
 AAOMG_API int mg_smooth(mg_handle h, const double* f, double* x, int steps, void* stream);
