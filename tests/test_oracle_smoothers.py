@@ -124,6 +124,24 @@ def test_colouring_is_distance_two(oracle_mod, L):
             assert (ip + 2 * jp) % 7 != (iq + 2 * jq) % 7
 
 
+@pytest.mark.parametrize("L", [3, 5, 7])
+def test_cgs_colouring_is_distance_one(oracle_mod, L):
+    """The CGS colours (i + j) mod 3 never couple two nodes of one colour in A
+    (so the 2x2 block solves of a colour are independent and each can gather
+    its residual from the current iterate), while (i - j) mod 3 would: its
+    colour is shared by the diagonal neighbours (i+1, j+1) of the "/" mesh."""
+    o = oracle_mod.Oracle(L, 1.0)
+    n1 = (1 << L) + 1
+    A = o.scipy(L, "M").tocoo()  # the coupling pattern of every block of A
+    bad_minus = 0
+    for p, q in zip(A.row, A.col):
+        if p != q:
+            ip, jp, iq, jq = p % n1, p // n1, q % n1, q // n1
+            assert (ip + jp) % 3 != (iq + jq) % 3
+            bad_minus += (ip - jp) % 3 == (iq - jq) % 3
+    assert bad_minus > 0
+
+
 @pytest.mark.parametrize("smoother", ["lsgs", "slsgs", "cgs"])
 def test_least_squares_functional_decreases(oracle_mod, smoother):
     """Each LSGS update minimises Phi(x) = 1/2 ||L^{-1/2}(f - A x)||^2 along one
