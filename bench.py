@@ -15,6 +15,11 @@ pinned host buffers (copies inside the timed region); roofline = the
 finest-level smoother sweeps (CUDA events inside the solve) against the
 measured HBM copy bandwidth; cpu_baseline = the FP64 CPU oracle on a bounded
 sample.  `--impl reference` times the CPU oracle alone on the same workload.
+
+Other modes (not timed against the reference): `--batch N` solves N
+independent instances of mixed size (levels 6..10, alpha log-uniform in
+[1e-8, 1]) at once through mg_solve_batch; `--protocol` prints the iteration
+counts of the paper's section 3 protocol in the layout of its Table 1.
 """
 from __future__ import annotations
 
