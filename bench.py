@@ -80,6 +80,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-vcycle", action="store_true", help="skip the V-cycle comparison")
     p.add_argument("--inner-cycles", type=int, default=0, help="FP32 cycles per refinement step (0: library default)")
+    p.add_argument("--autotune", action="store_true",
+                   help="let the library time each level's candidate kernels at set-up")
     p.add_argument("--batch", type=int, default=0,
                    help="time N independent instances of mixed size through mg_solve_batch instead")
     p.add_argument("--protocol", action="store_true",
@@ -200,7 +202,8 @@ def run_ours(args, rank, world, local):
 
     def make(precision, profile):
         return {a: mg.Solver(L, a, smoother=args.smoother, precision=precision, cycle=args.cycle, max_iter=100,
-                             profile=profile, inner_cycles=args.inner_cycles) for a in ALPHAS}
+                             profile=profile, inner_cycles=args.inner_cycles, autotune=args.autotune)
+                for a in ALPHAS}
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
@@ -345,7 +348,8 @@ def run_ours(args, rank, world, local):
                       "level": L, "unknowns_per_solve": 2 * N, "solves_per_step": len(ALPHAS),
                       "smoother": args.smoother, "cycle": args.cycle, "precision": "fp32_refine",
                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
-                      "concurrency": 1 if args.serial else len(ALPHAS)},
+                      "concurrency": 1 if args.serial else len(ALPHAS),
+                      "kernels": "autotuned at set-up" if args.autotune else "measured defaults"},
            "iterations": {str(a): its32[a] for a in ALPHAS},
            "roofline": roofline, "roofline_by_time": by_time, "clocks": clocks, "gpu_launches": launches}
 
@@ -565,7 +569,7 @@ def run_batch(args):
     levels, alphas, yds = inputs.batch_instances(args.batch, 2)
     t0 = time.time()
     solvers = [mg.Solver(L, a, smoother=args.smoother, precision="fp32_refine", cycle=args.cycle, max_iter=100,
-                         inner_cycles=args.inner_cycles) for L, a in zip(levels, alphas)]
+                         inner_cycles=args.inner_cycles, autotune=args.autotune) for L, a in zip(levels, alphas)]
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     fs = [s.rhs_from_yd(torch.tensor(y, dtype=torch.float64, device="cuda")) for s, y in zip(solvers, yds)]

@@ -97,11 +97,15 @@ typedef struct mg_options {
     int small_max;    /* levels with at most this many nodes per side smooth in one launch per
                          smoothing call (one block or one cluster); 0: 257; < 0: never */
     int cluster_size; /* blocks per cluster of that launch on levels with 65, 129 or 257 nodes per
-                         side (2..16); 0: by level size and precision (FP32: one block, 8, 16;
+                         side (2..16); 0: by level size and precision (FP32: one block, 16, 16;
                          FP64: 8, 16, 16); 1: one block where it fits, else a launch per colour
                          phase.  A size that cannot run: BAD_ARG */
     int profile_level; /* with profile = 1: the level whose smoothing calls are timed; <= 0 or
                           > levels: the finest */
+    int autotune;     /* 1: at set-up, time the candidate smoothing kernels of every level and keep
+                         the fastest (one block or each cluster size that can run on levels up to
+                         small_max nodes per side, unless cluster_size forces one; for LSGS above,
+                         the one-launch step against a launch per colour phase); 0: the defaults */
 } mg_options;
 
 /* Build the hierarchy for h = 2^-levels (1 <= levels <= 13; level 1 is the
@@ -183,6 +187,16 @@ AAOMG_API int mg_control(mg_handle h, const double* x, double* u, void* stream);
  * receives the adjoint state.  Device pointers except dalpha (host). */
 AAOMG_API int mg_adjoint(mg_handle h, const double* x, const double* ubar, double* z, double* gyD, double* dalpha,
                          double tol, void* stream);
+
+/* The kernel that smooths level `level` (1..levels) inside the handle's cycle,
+ * as chosen at set-up (defaults, options or autotuning): *kind is MG_KERNEL_*, *blocks
+ * (may be NULL) the blocks per launch for STRIPS (1: one block, else the
+ * cluster size) and BAND (the tiles), else 0. */
+#define MG_KERNEL_PHASES 0 /* one launch per colour phase (per residual and update for NE) */
+#define MG_KERNEL_STRIPS 1 /* whole smoothing call in one launch of one block or one cluster */
+#define MG_KERNEL_BAND 2   /* one launch per LSGS step, wavefront over bands and segments */
+#define MG_KERNEL_COARSE 3 /* no smoothing kernel: coarsest solve, dense coarse map or single-block cycle */
+AAOMG_API int mg_level_kernel(mg_handle h, int level, int* kind, int* blocks);
 
 /* ||x||_L and ||x||_{L^-1} of a vector x (2N doubles, device) on the finest
  * level, with L = diag(Q) of the paper's block preconditioner (section 2):

@@ -51,6 +51,7 @@ class Options(ctypes.Structure):
         ("small_max", ctypes.c_int),
         ("cluster_size", ctypes.c_int),
         ("profile_level", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -86,6 +87,7 @@ def load():
             "mg_solve_host": (I, [H, P, P, D, pI, pD, P]),
             "mg_get_history": (I, [H, pD, I, pI]),
             "mg_norms": (I, [H, P, pD, pD, P]),
+            "mg_level_kernel": (I, [H, I, pI, pI]),
             "mg_kernel_launches": (ctypes.c_longlong, [H]),
             "mg_get_profile": (I, [H, pD, ctypes.POINTER(ctypes.c_longlong)]),
             "mg_reset_profile": (I, [H]),
@@ -163,14 +165,14 @@ class Solver:
                  cycle: str = "W", nu_pre: int = 0, nu_post: int = 0, tau: float = 0.0, k_variant: int = 0,
                  max_iter: int = 0, inner_cycles: int = 0, coarse_level: int = -1, profile: bool = False,
                  tile_w: int = 0, tile_h: int = 0, small_max: int = 0, cluster_size: int = 0,
-                 profile_level: int = 0):
+                 profile_level: int = 0, autotune: bool = False):
         self._lib = load()
         self.levels, self.alpha = int(levels), float(alpha)
         self.smoother, self.precision, self.cycle_kind = smoother, precision, cycle
         opt = Options(SMOOTHER[smoother], int(nu_pre), int(nu_post), CYCLE[cycle], PRECISION[precision],
                       float(tau), int(k_variant), int(max_iter), int(inner_cycles), int(coarse_level),
                       int(bool(profile)), int(tile_w), int(tile_h), int(small_max), int(cluster_size),
-                      int(profile_level))
+                      int(profile_level), int(bool(autotune)))
         h = ctypes.c_void_p()
         _check(self._lib.mg_setup(self.levels, self.alpha, ctypes.byref(opt), ctypes.byref(h)), "mg_setup")
         self._h = h
@@ -238,6 +240,17 @@ class Solver:
         if raise_on_fail:
             _check(code, "mg_solve")
         return it.value, rr.value, code
+
+    def level_kernels(self):
+        """{level: (kind, blocks)} for levels 1..L: kind 'phases', 'strips',
+        'band' or 'coarse', blocks as returned by mg_level_kernel."""
+        names = {0: "phases", 1: "strips", 2: "band", 3: "coarse"}
+        out = {}
+        for l in range(1, self.levels + 1):
+            k, b = ctypes.c_int(), ctypes.c_int()
+            _check(self._lib.mg_level_kernel(self._h, l, ctypes.byref(k), ctypes.byref(b)), "mg_level_kernel")
+            out[l] = (names[k.value], b.value)
+        return out
 
     def norms(self, x):
         """(||x||_L, ||x||_{L^-1}) on the finest level (the paper's L = diag(Q))."""

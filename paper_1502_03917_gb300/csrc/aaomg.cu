@@ -44,6 +44,7 @@ struct Lev {
     void* rh = nullptr;
     BandGrid bg{};
     int cs = 0;              // smoothing calls in one launch: of one block (1) or a cluster of cs blocks; 0: no
+    bool band = false;       // LSGS steps by the one-launch band kernel (else one launch per colour phase)
     void* ctab = nullptr;    // its boundary-class table (EdgeClass[25] in the cycles' precision)
     LevelP<float> pf{};
     LevelP<double> pd{};
@@ -203,7 +204,7 @@ struct mg_ctx {
     mg_options o{};
     int dev = 0;
     int nsm = 152;
-    int band_min = 513;       // FP32 levels with at least this many nodes per side use the one-launch LSGS step
+    int band_min = 1025;      // FP32 levels with at least this many nodes per side use the one-launch LSGS step
     int small_max = 257;      // levels up to this many nodes per side: one launch per smoothing call
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
@@ -309,7 +310,7 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
         }
         break;
     case MG_SMOOTHER_LSGS: {
-        if (v.n + 1 < H->band_min) goto phases;
+        if (!v.band) goto phases;
         // one launch per step, ping-pong between x and x2
         T* a = x;
         T* b = (T*)v.x2;
@@ -444,12 +445,66 @@ int build_class_table(mg_ctx* H, Lev& v, double km) {
     return AAOMG_OK;
 }
 
+// Autotuning: for every level, time the candidate smoothing kernels on the
+// level's own (zero) vectors -- a single block and every cluster size that can
+// run on levels up to small_max nodes per side; the band kernel against one
+// launch per colour phase for LSGS above -- and keep the fastest.  A call of 2
+// steps, once to warm up and then three times under CUDA events.
+template <typename T>
+int autotune_levels(mg_ctx* H, double km) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    int rc = AAOMG_OK;
+    auto timed = [&](auto&& call) -> float {
+        call();
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 3; ++r) call();
+        cudaEventRecord(b, s);
+        float ms = -1.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess)
+            return -1.f;
+        return ms;
+    };
+    for (int l = 2; l <= H->L && !rc; ++l) {
+        Lev& v = H->lev[l];
+        if (v.n + 1 <= H->small_max && H->o.cluster_size == 0) {
+            if (!v.ctab && (rc = build_class_table<T>(H, v, km))) break;
+            float best = -1.f;
+            int best_cs = v.cs;
+            for (int cs : {1, 2, 4, 8, 16}) {
+                if (strips_max_active<T>(v.n, cs) <= 0) continue;
+                v.cs = cs;
+                const float ms = timed([&] { smooth<T>(H, l, 2, s); });
+                if (ms >= 0.f && (best < 0.f || ms < best)) {
+                    best = ms;
+                    best_cs = cs;
+                }
+            }
+            v.cs = best_cs;
+        } else if (v.cs == 0 && H->o.smoother == MG_SMOOTHER_LSGS && H->o.tile_w <= 0 && H->o.tile_h <= 0) {
+            v.band = true;
+            const float tb = timed([&] { smooth<T>(H, l, 2, s); });
+            v.band = false;
+            const float tp = timed([&] { smooth<T>(H, l, 2, s); });
+            v.band = tb >= 0.f && (tp < 0.f || tb < tp);
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(s);
+    if (!rc && cudaGetLastError() != cudaSuccess) rc = fail(AAOMG_ERR_CUDA, "autotuning launch failed");
+    return rc;
+}
+
 // blocks of the one-launch smoothing call by level size and precision,
 // measured on GB300 (1: a single block)
 int default_cluster(int n, bool fp32) {
     if (n <= 32) return 1;
     if (n <= 64) return fp32 ? 1 : 8;
-    if (n <= 128) return fp32 ? 8 : 16;
     return 16;
 }
 
@@ -698,9 +753,11 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         H->band_min = 0;
         H->small_max = -1;
     } else if (H->fp32) {
-        // measured per LSGS step against the per-phase launches: 69 vs 86 us
-        // at 513^2, 84 vs 144 us at 1025^2, 156 vs 402 us at 2049^2
-        H->band_min = H->small_max + 1 > 513 ? H->small_max + 1 : 513;
+        // measured per LSGS step against the per-phase launches: 84 vs 144 us
+        // at 1025^2, 156 vs 402 us at 2049^2; at 513^2 the autotuner's
+        // smoothing calls and the five-solve bench favour the per-phase
+        // launches (the band step holds every SM while its blocks run)
+        H->band_min = H->small_max + 1 > 1025 ? H->small_max + 1 : 1025;
     } else {
         // FP64: the one-launch step's per-node arithmetic is bound by GB300's
         // FP64 rate (about 1/64 of FP32); the per-phase launches, which spread
@@ -740,6 +797,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         CK(cudaMemset(v.x, 0, bytes));
         CK(cudaMemset(v.x2, 0, bytes));
         v.bg = H->fp32 ? band_grid<float>(v.n, o.tile_w, o.tile_h, H->nsm) : band_grid<double>(v.n, o.tile_w, o.tile_h, H->nsm);
+        v.band = v.n + 1 >= H->band_min;
         CK(cudaMemset(v.f, 0, bytes));
         CK(cudaMemset(v.rh, 0, bytes));
         v.pd = make_params<double>(v.n, v.ld, v.fs, alpha, false, km, o.tau);
@@ -775,6 +833,7 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         if (!rc && v.cs > 0)
             rc = H->fp32 ? build_class_table<float>(H, v, km) : build_class_table<double>(H, v, km);
     }
+    if (!rc && o.autotune) rc = H->fp32 ? autotune_levels<float>(H, km) : autotune_levels<double>(H, km);
     if (rc) {
         mg_destroy(H);
         return rc;
@@ -870,6 +929,26 @@ int mg_residual(mg_handle h, const double* f, const double* x, double* r, double
         double fn = h->h_red[1] > 0.0 ? h->h_red[1] : 1.0;
         *relres = std::sqrt(h->h_red[0] / fn);
     }
+    return AAOMG_OK;
+}
+
+int mg_level_kernel(mg_handle h, int level, int* kind, int* blocks) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (level < 1 || level > h->L || !kind) return fail(AAOMG_ERR_BAD_ARG, "level out of range or null output");
+    const Lev& v = h->lev[level];
+    int k = MG_KERNEL_PHASES, b = 0;
+    if (level == 1 || level <= h->lc || (h->ld > 0 && level <= h->ld)) {
+        k = MG_KERNEL_COARSE;
+    } else if (v.cs > 0) {
+        k = MG_KERNEL_STRIPS;
+        b = v.cs;
+    } else if (v.band && h->o.smoother == MG_SMOOTHER_LSGS) {
+        k = MG_KERNEL_BAND;
+        b = v.bg.nb * v.bg.ns;
+    }
+    *kind = k;
+    if (blocks) *blocks = b;
     return AAOMG_OK;
 }
 

@@ -101,6 +101,35 @@ def test_cluster_smoothing_call(mg, oracle_mod, L, cs, smoother, precision):
             assert d <= TOL[precision], (steps, d)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("smoother", ["lsgs", "cgs"])
+def test_autotuned_kernels(mg, oracle_mod, smoother, precision):
+    """With autotune the set-up picks each level's kernel by timing; whatever
+    it picks, a smoothing call still gives the oracle's steps and a solve the
+    oracle's solution."""
+    L, alpha = 9, 1e-2
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 900))
+    f = inputs.f32_exact(inputs.x_uniform(L, 901))
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother)
+    with mg.Solver(L, alpha, smoother=smoother, precision=precision, autotune=True) as s:
+        x = dev(x0)
+        s.smooth(dev(f), x, 2)
+        d = field_reldiff(host(x), o.smooth(f, x0, 2), o.nn())
+        assert d <= TOL[precision], d
+        yD = inputs.yd_uniform(L, 0)
+        fs = s.rhs_from_yd(dev(yD))
+        xs = torch.zeros_like(fs)
+        it, rr, code = s.solve(fs, xs, tol=1e-10)
+        assert code == 0 and rr <= 1e-10
+        kinds = s.level_kernels()
+        assert all(kinds[l][0] == "coarse" for l in range(1, 6))
+        assert all(kinds[l][0] in ("strips", "band", "phases") for l in range(6, L + 1))
+    with mg.Solver(L, alpha, smoother=smoother, precision=precision) as s:
+        xd = torch.zeros_like(fs)
+        s.solve(s.rhs_from_yd(dev(yD)), xd, tol=1e-10)
+    assert field_reldiff(host(xs), host(xd), o.nn()) <= 1e-8
+
+
 @pytest.mark.parametrize("L,cs", [(8, 2), (7, 17), (6, 64)])
 def test_cluster_size_that_cannot_run(mg, L, cs):
     """A forced cluster size whose strips do not fit in shared memory, or that
@@ -289,6 +318,19 @@ def test_protocol_iterations_match_oracle(mg, oracle_mod, k, alpha, smoother):
     with mg.Solver(k, alpha, smoother=smoother, precision="fp64", nu_pre=nu, nu_post=nu) as s:
         got = s.protocol_iterations(dev(x0), 1e-6, 300)
     assert got == want > 0
+
+
+def test_default_level_kernels(mg):
+    """The per-level kernels of the default FP32 LSGS configuration at
+    h = 2^-11: the dense level-5 map below, one block on level 6, clusters of
+    16 blocks on levels 7 and 8, per-phase launches on level 9, the band kernel
+    on levels 10 and 11 (the choices the set-up autotuner makes on GB300)."""
+    with mg.Solver(11, 1e-2, smoother="lsgs", precision="fp32_refine") as s:
+        k = s.level_kernels()
+    assert [k[l][0] for l in range(1, 6)] == ["coarse"] * 5
+    assert k[6] == ("strips", 1) and k[7] == ("strips", 16) and k[8] == ("strips", 16)
+    assert k[9] == ("phases", 0)
+    assert all(k[l][0] == "band" and k[l][1] > 0 for l in (10, 11))
 
 
 def test_profile_of_one_level(mg):
