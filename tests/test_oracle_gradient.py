@@ -49,3 +49,19 @@ def test_adjoint_gradient_matches_finite_differences(oracle_mod, alpha):
     fa = (loss_and_grad(oracle_mod, L, alpha * np.exp(h), yD, ut, False) -
           loss_and_grad(oracle_mod, L, alpha * np.exp(-h), yD, ut, False)) / (2 * h)
     assert alpha * g_alpha == pytest.approx(fa, rel=1e-6)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1e-4])
+def test_symmetric_adjoint_identity(oracle_mod, alpha):
+    """The backward pass solves with A itself because A is symmetric: for any
+    right-hand sides f, g the oracle's multigrid solutions satisfy
+    g . A^{-1} f = f . A^{-1} g (to the solves' tolerance)."""
+    L = 4
+    o = oracle_mod.Oracle(L, alpha)
+    rng = np.random.default_rng(21)
+    n2 = 2 * o.nn()
+    f, g = rng.standard_normal(n2), rng.standard_normal(n2)
+    xf, _, rf, _ = o.solve(f, tol=1e-13, max_iter=400)
+    xg, _, rg, _ = o.solve(g, tol=1e-13, max_iter=400)
+    assert rf <= 1e-13 and rg <= 1e-13
+    assert g @ xf == pytest.approx(f @ xg, rel=1e-9)
