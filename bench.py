@@ -91,6 +91,10 @@ def parse():
                         "nvidia-smi sampling (roofline and clocks are then not reported)")
     p.add_argument("--serial", action="store_true",
                    help="solve the alphas one after another instead of concurrently on separate streams")
+    p.add_argument("--no-l12", action="store_true", help="skip the h = 2^-12 single-instance line")
+    p.add_argument("--profile-band", type=int, default=0, metavar="L",
+                   help="for ncu captures: set up one FP32 LSGS handle at h = 2^-L and run --steps finest-level "
+                        "smoothing steps (mg_smooth) after --warmup untimed ones; prints the CUDA-event time")
     return p.parse_args()
 
 
@@ -295,23 +299,23 @@ def run_ours(args, rank, world, local):
     N = ((1 << L) + 1) ** 2
     unknowns_step = len(ALPHAS) * 2 * N
 
-    sol32 = make("fp32_refine", not args.profiling_run)
+    sol32 = make("fp32_refine", False)
     ms, its32, launches, prof, clocks, xs32 = timed_steps(sol32, K, W)
     ms = max_over_ranks(ms)
     value = job_value(unknowns_step, K, world, ms)
 
-    # roofline of the dominant kernel: the finest-level smoother sweeps
+    # roofline of the finest-level smoother sweep, timed with nothing else in
+    # flight (one solve, in-graph CUDA events around each finest-level call)
     pk = peaks()
-    sm_ms = sum(p[0] for p in prof)
-    sweeps = sum(p[1] for p in prof)
-    achieved = SWEEP_BYTES_FP32 * N * sweeps / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
     peak = pk["hbm_gbs"] if pk else 6800.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": band_traffic(L),
-                "kernel": "finest-level LSGS smoothing sweep (FP32)",
-                "peak_source": "measured" if pk else "fallback",
-                "sweep_ms": sm_ms / sweeps if sweeps else None,
-                "share_of_step": sm_ms / ms if ms else None}
+    roofline = None
+    if not args.profiling_run:
+        roofline = sweep_roofline(mg, L, yD, 1e-4, args, peak, pk is not None)
+        # share of the timed steps: the isolated sweep time times the finest
+        # sweeps the timed solves ran (refinement steps x inner cycles x 4)
+        per_iter = roofline.pop("sweeps_per_iteration")
+        sweeps = per_iter * sum(its32.values()) * K
+        roofline["share_of_step"] = roofline["sweep_ms"] * sweeps / ms if roofline["sweep_ms"] else None
 
     # By device time the W-cycle is dominated by the latency-bound one-launch
     # smoothing calls on level 6 (the top kernel of the ncu launch list): time
@@ -353,6 +357,11 @@ def run_ours(args, rank, world, local):
            "iterations": {str(a): its32[a] for a in ALPHAS},
            "roofline": roofline, "roofline_by_time": by_time, "clocks": clocks, "gpu_launches": launches}
 
+    out["error_vs_oracle"] = error_vs_golden(L, {a: xs32[a] for a in ALPHAS}, args.smoother)
+
+    if not args.no_l12 and L == 11 and not args.profiling_run:
+        out["l12"] = run_l12(args, mg, peak, pk is not None, flush)
+
     if not args.no_fp64:
         sol64 = make("fp64", False)
         K64 = max(1, min(K, 2))
@@ -391,6 +400,151 @@ def run_ours(args, rank, world, local):
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def sweep_roofline(mg, L, yD, alpha, args, peak, measured):
+    """The finest-level LSGS sweep timed with nothing else in flight: one solve
+    (after a warm-up solve) with CUDA events recorded inside the solver's graph
+    around every finest-level smoothing call; 24 algorithmic bytes per node and
+    sweep against the measured HBM copy bandwidth."""
+    import torch
+
+    s = mg.Solver(L, alpha, smoother=args.smoother, precision="fp32_refine", cycle=args.cycle, max_iter=100,
+                  profile=True, inner_cycles=args.inner_cycles, autotune=args.autotune)
+    f = s.rhs_from_yd(yD)
+    x = torch.zeros_like(f)
+    s.solve(f, x, tol=args.tol)
+    s.reset_profile()
+    x.zero_()
+    it, _, _ = s.solve(f, x, tol=args.tol)
+    t_ms, nsw = s.profile()
+    s.close()
+    N = ((1 << L) + 1) ** 2
+    sweep_ms = t_ms / nsw if nsw else None
+    achieved = SWEEP_BYTES_FP32 * N / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": band_traffic(L),
+            "kernel": f"finest-level LSGS smoothing sweep (FP32, h=2^-{L}, {(1 << L) + 1}^2 nodes)",
+            "peak_source": "measured" if measured else "fallback", "sweep_ms": sweep_ms, "sweeps_timed": nsw,
+            "algorithmic_bytes_per_sweep": SWEEP_BYTES_FP32 * N,
+            "timing": f"one solve alone (alpha={alpha:g}), CUDA events in the solver graph around each "
+                      "finest-level smoothing call",
+            "sweeps_per_iteration": nsw / it if it else 0}
+
+
+def error_vs_golden(L, xs, smoother):
+    """Element-wise error of GPU solutions against the FP64 oracle's at the
+    sampled nodes of tests/golden/oracle_L{L}.json (written by the oracle
+    alone): max |x - x_oracle| / max |x_oracle| over y and lambda, per alpha."""
+    try:
+        g = json.load(open(GOLDEN.format(L=L)))
+    except (OSError, ValueError):
+        return None
+    import numpy as np
+
+    idx = np.array(g["sample_nodes"])
+    nn = ((1 << L) + 1) ** 2
+    out = {}
+    for a, x in xs.items():
+        ref = next((r for r in g["runs"] if r["smoother"] == smoother and r["alpha"] == a), None)
+        if ref is None:
+            continue
+        xh = x.cpu().numpy()
+        e = 0.0
+        for got, want in ((xh[idx], np.array(ref["y"])), (xh[nn + idx], np.array(ref["lambda"]))):
+            e = max(e, float(np.abs(got - want).max() / np.abs(want).max()))
+        out[str(a)] = e
+    return out
+
+
+def run_l12(args, mg, peak, measured, flush):
+    """The largest single instance: h = 2^-12 (4097^2 nodes, 33.6M unknowns),
+    alpha = 1e-6, y_D = +-1 piecewise constant plus U(-0.05, 0.05) noise (seed
+    5); one solve at a time to the tolerance, FP32+refine against plain FP64,
+    each solution's error against the FP64 oracle, and the finest sweep's
+    roofline (at this size x and f, 268 MB, exceed the 129 MB L2)."""
+    import torch
+
+    from paper_1502_03917_gb300 import inputs
+
+    L, a = 12, 1e-6
+    N = ((1 << L) + 1) ** 2
+    yD = torch.tensor(inputs.yd_piecewise(L, 5), dtype=torch.float64, device="cuda")
+
+    def timed(precision, K):
+        s = mg.Solver(L, a, smoother=args.smoother, precision=precision, cycle=args.cycle, max_iter=100,
+                      inner_cycles=args.inner_cycles)
+        f = s.rhs_from_yd(yD)
+        x = torch.zeros_like(f)
+        s.solve(f, x, tol=args.tol)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        it = rr = None
+        for k in range(K):
+            flush.fill_(float(k))
+            x.zero_()
+            ev[k][0].record()
+            it, rr, _ = s.solve(f, x, tol=args.tol)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / K
+        err = error_vs_golden(L, {a: x}, args.smoother)
+        s.close()
+        return {"value": 2 * N / (ms / 1e3), "ms_per_solve": ms, "iterations": it, "relres": rr,
+                "error_vs_oracle": err.get(str(a)) if err else None, "solves_timed": K}
+
+    out = {"workload": f"Poisson control, h=2^-{L} ({(1 << L) + 1}^2 nodes, {2 * N} unknowns), alpha={a:g}, "
+                       f"y_D=+-1 piecewise + U(-0.05,0.05) seed 5, {args.smoother.upper()} {args.cycle}(2,2) to "
+                       f"h=1/2, tol {args.tol}, one solve at a time, L2 flushed before each",
+           "unit": UNIT}
+    out["fp32_refine"] = timed("fp32_refine", 3)
+    out["fp64_plain"] = timed("fp64", 1)
+    out["roofline"] = sweep_roofline(mg, L, yD, a, args, peak, measured)
+    out["roofline"].pop("sweeps_per_iteration", None)
+    return out
+
+
+def run_profile_band(args):
+    """A small, self-contained launch sequence for ncu: one FP32 LSGS handle
+    at h = 2^-L with the default kernels (the band kernel on the finest level
+    from 1025^2 nodes), `warmup` + `steps` finest-level smoothing steps through
+    mg_smooth, one step per call."""
+    import torch
+
+    from paper_1502_03917_gb300 import build as B
+    from paper_1502_03917_gb300 import inputs
+    import paper_1502_03917_gb300.aaomg as mg
+
+    B.build()
+    L = args.profile_band
+    with mg.Solver(L, 1e-4, smoother="lsgs", precision="fp32_refine") as s:
+        f = torch.tensor(inputs.x_uniform(L, 1), dtype=torch.float64, device="cuda")
+        x = torch.tensor(inputs.x_uniform(L, 2), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            s.smooth(f, x, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            s.smooth(f, x, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_band": L, "kernels": s.level_kernels()[L], "steps": args.steps,
+                          "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps),
+                          "note": "one mg_smooth call = FP64->FP32 conversion, one LSGS step, FP32->FP64"}))
+
+
+def host_cpu():
+    """The host's core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        outp = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in outp.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
 
 
 def run_e2e(args, solvers, yD, K, world, max_over_ranks, run_all):
@@ -463,7 +617,7 @@ def cpu_baseline(L, args, its_gpu=None):
     N = ((1 << L) + 1) ** 2
     total_it = sum(its.values()) if its else None
     value = len(ALPHAS) * 2 * N / (t_cycle * total_it) if total_it else None
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"one {args.smoother.upper()} {args.cycle}(2,2) cycle at h=2^-{L}, alpha=1e-4, from x=0 "
                       f"({t_cycle:.2f} s), scaled by the oracle's iteration counts to {args.tol} for the five "
                       f"alphas ({total_it} cycles); assembly excluded",
@@ -487,10 +641,12 @@ def run_reference(args, rank, world):
         print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration counts for h=2^-{L}"}))
         return
     yD = inputs.yd_sine_noise(L, 1)
-    # one oracle W-cycle per step, alphas in turn; each step stands for one
-    # solve: (cycle time) x (iterations the oracle needs for that alpha)
+    # Each step is one oracle W-cycle at full size, alphas in turn, timed as it
+    # runs; a cycle does 1/iterations of that alpha's solve, so a step counts
+    # 2N / iterations solved unknowns (the value is projected from measured
+    # cycle times: a whole oracle solve at this size takes minutes).
     hier = {}
-    times = []
+    times, units = [], []
     for k in range(args.warmup + args.steps):
         a = ALPHAS[k % len(ALPHAS)]
         if a not in hier:
@@ -502,17 +658,23 @@ def run_reference(args, rank, world):
         o.cycle(f, x)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
-            times.append(dt * its[str(a)])
+            times.append(dt)
+            units.append(2 * N / its[str(a)])
+    for o, _ in hier.values():
+        o.close()
     sec = sum(times)
-    value = args.steps * 2 * N / sec
+    value = sum(units) / sec
+    host = host_cpu()
+    sample = ("per step one oracle W-cycle at full size (alphas in turn), measured; it counts as 1/iterations of "
+              "that alpha's solve (iterations from tests/golden), so the value is projected from cycle times")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "projected": True,
            "config": {"workload": f"Poisson control, h=2^-{L}, alpha in {ALPHAS}, {args.smoother.upper()} "
                                   f"{args.cycle}(2,2), FP64 CPU oracle", "level": L},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "per step one oracle cycle at full size, scaled by the oracle's iteration "
-                                      "count for that alpha"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host,
+                            "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -608,7 +770,10 @@ def run_batch(args):
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.batch:
+    if args.profile_band:
+        if rank == 0:
+            run_profile_band(args)
+    elif args.batch:
         if rank == 0:
             run_batch(args)
     elif args.protocol:

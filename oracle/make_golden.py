@@ -1,15 +1,21 @@
-"""Write tests/golden/oracle_L11.json: full-size reference values computed by
+"""Write tests/golden/oracle_L{L}.json: full-size reference values computed by
 the oracle alone (nothing here touches the CUDA path).
 
-Workload: Poisson control on the unit square at h = 2^-11 (2049 x 2049 nodes,
-8.4M unknowns), y_D = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1) (seed 1), W-cycle
-with 2+2 smoothing steps down to h = 1/2, for alpha in {1, 1e-2, 1e-4, 1e-6,
-1e-8} and the NE and LSGS smoothers.  Each solve runs to a relative residual of
-1e-10 (at this size FP64 rounding stalls the residual near 3e-11 for alpha = 1);
-the file keeps the residual history (so the iteration count to any tolerance
-above 1e-10 can be read off), and the solution at 256 seeded node indices.
+Workloads (W-cycle with 2+2 smoothing steps down to h = 1/2):
 
-Usage: python oracle/make_golden.py [L]   (takes tens of minutes on one core)
+* L = 11 (default), the scaling workload at its largest size: h = 2^-11
+  (2049 x 2049 nodes, 8.4M unknowns), y_D = sin(2 pi x) sin(2 pi y) +
+  0.1 N(0,1) (seed 1), alpha in {1, 1e-2, 1e-4, 1e-6, 1e-8}, NE and LSGS.
+* L = 12, the largest single instance: h = 2^-12 (4097 x 4097 nodes, 33.6M
+  unknowns), y_D = +1 on [0.25, 0.75]^2, -1 elsewhere, plus U(-0.05, 0.05)
+  noise (seed 5), alpha = 1e-6, LSGS.
+
+Each solve runs to a relative residual of 1e-10 (at these sizes FP64 rounding
+stalls the residual a little below that); the file keeps the residual history
+(so the iteration count to any tolerance above 1e-10 can be read off), and the
+solution at 256 seeded node indices.
+
+Usage: python oracle/make_golden.py [L]   (tens of minutes per solve on one core)
 """
 import json
 import os
@@ -24,19 +30,26 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 from paper_1502_03917_gb300 import inputs  # noqa: E402
 
-ALPHAS = [1.0, 1e-2, 1e-4, 1e-6, 1e-8]
+WORKLOADS = {
+    11: {"workload": "y_D = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1), seed 1; W(2,2) to h=1/2",
+         "yd": lambda L: inputs.yd_sine_noise(L, 1),
+         "alphas": [1.0, 1e-2, 1e-4, 1e-6, 1e-8], "smoothers": ("lsgs", "ne")},
+    12: {"workload": "y_D = +1 on [0.25,0.75]^2, -1 elsewhere, + U(-0.05,0.05), seed 5; W(2,2) to h=1/2",
+         "yd": lambda L: inputs.yd_piecewise(L, 5),
+         "alphas": [1e-6], "smoothers": ("lsgs",)},
+}
 
 
 def main():
     L = int(sys.argv[1]) if len(sys.argv) > 1 else 11
+    w = WORKLOADS[L]
     out = os.path.join(ROOT, "tests", "golden", f"oracle_L{L}.json")
-    yD = inputs.yd_sine_noise(L, 1)
+    yD = w["yd"](L)
     nn = ((1 << L) + 1) ** 2
     sample = np.sort(np.random.default_rng(12345).choice(nn, size=256, replace=False))
-    res = {"level": L, "workload": "y_D = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1), seed 1; W(2,2) to h=1/2",
-           "sample_nodes": sample.tolist(), "runs": []}
-    for smoother in ("lsgs", "ne"):
-        for a in ALPHAS:
+    res = {"level": L, "workload": w["workload"], "sample_nodes": sample.tolist(), "runs": []}
+    for smoother in w["smoothers"]:
+        for a in w["alphas"]:
             t0 = time.time()
             o = oracle.Oracle(L, a, smoother=smoother)
             f = o.rhs(yD)

@@ -137,8 +137,12 @@ def residual_noalloc(levels: int, alpha: float, f, x, r=None, k_variant: int = 0
     N = ((1 << int(levels)) + 1) ** 2
     rr = ctypes.c_double()
     rp = _dptr(r, 2 * N) if r is not None else None
-    _check(lib.mg_residual_noalloc(int(levels), float(alpha), int(k_variant), _dptr(f, 2 * N), _dptr(x, 2 * N), rp,
-                                   ctypes.byref(rr), _stream()), "mg_residual_noalloc")
+    code = lib.mg_residual_noalloc(int(levels), float(alpha), int(k_variant), _dptr(f, 2 * N), _dptr(x, 2 * N), rp,
+                                   ctypes.byref(rr), _stream())
+    if code != OK:
+        # this entry point records no message: mg_last_error() would still hold
+        # an earlier, unrelated failure of this thread
+        raise MGError(code, "mg_residual_noalloc", lib.mg_strerror(code).decode())
     return rr.value
 
 

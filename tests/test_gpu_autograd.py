@@ -3,8 +3,8 @@
 * autograd gradients of L = 1/2 ||u - u_t||^2 (u = lambda / alpha) equal the
   direct-solve gradient built from the oracle's matrices at h = 2^-5;
 * they agree with central finite differences of the GPU solve (FP64, step 1e-6);
-* mg_solve_batch on independent problems gives every instance the result of
-  its own mg_solve.
+* mg_solve_batch on independent problems of mixed size and precision gives
+  every instance the oracle's solution (and bitwise its own mg_solve's).
 """
 import numpy as np
 import pytest
@@ -78,19 +78,33 @@ def test_autograd_finite_differences():
     assert la.grad.item() == pytest.approx(fd_a, rel=1e-6)
 
 
-def test_batch_solve_equals_individual_solves():
+def test_batch_solve_against_oracle(oracle_mod):
+    """Every instance of a mixed batch (levels 3..8, alpha log-uniform in
+    [1e-8, 1], both precisions) solved through mg_solve_batch equals the FP64
+    oracle's multigrid solution to 1e-8 (the L norm of the error and the
+    element-wise maximum of y and of u = lambda / alpha); it is also bitwise the
+    result of the instance's own mg_solve."""
     import paper_1502_03917_gb300.aaomg as mg
 
-    levels, alphas, yds = inputs.batch_instances(6, 2, lmin=3, lmax=8)
-    precs = ["fp32_refine", "fp64"] * 3
-    solvers = [mg.Solver(L, a, smoother="lsgs", precision=p) for L, a, p in zip(levels, alphas, precs)]
+    levels, alphas, yds = inputs.batch_instances(10, 2, lmin=3, lmax=8)
+    precs = ["fp32_refine", "fp64"] * 5
+    solvers = [mg.Solver(L, a, smoother="lsgs", precision=p, max_iter=200) for L, a, p in zip(levels, alphas, precs)]
     fs = [s.rhs_from_yd(dev(y)) for s, y in zip(solvers, yds)]
     xs = [torch.zeros_like(f) for f in fs]
-    its, rrs, code = mg.solve_batch(solvers, fs, xs, tol=1e-10)
-    assert code == mg.OK and all(r <= 1e-10 for r in rrs)
-    for s, f, x, it in zip(solvers, fs, xs, its):
+    its, rrs, code = mg.solve_batch(solvers, fs, xs, tol=1e-11)
+    assert code == mg.OK and all(r <= 1e-11 for r in rrs)
+    for s, L, a, y, f, x, it in zip(solvers, levels, alphas, yds, fs, xs, its):
+        o = oracle_mod.Oracle(L, a, smoother="lsgs")
+        xo, _, _, _ = o.solve(o.rhs(y), tol=1e-13, max_iter=400)
+        xg = x.cpu().numpy()
+        n = o.nn()
+        eL = o.norm_L(xg - xo) / o.norm_L(xo)
+        ey = np.abs(xg[:n] - xo[:n]).max() / np.abs(xo[:n]).max()
+        eu = np.abs(xg[n:] - xo[n:]).max() / np.abs(xo[n:]).max()
+        assert max(eL, ey, eu) <= 1e-8, (L, a, s.precision, eL, ey, eu)
+        o.close()
         x1 = torch.zeros_like(f)
-        it1, rr1, _ = s.solve(f, x1, tol=1e-10)
+        it1, rr1, _ = s.solve(f, x1, tol=1e-11)
         assert it1 == it
         assert torch.equal(x1, x)
     for s in solvers:

@@ -1,5 +1,7 @@
 """GPU parity: every step of the CUDA path against the FP64 oracle, through the
-C ABI, element by element, on seeded inputs.
+C ABI, element by element, on seeded inputs: every comparison bounds both the
+normwise relative difference of each field and its element-wise maximum
+relative to the field's largest entry.
 
 Tolerances: FP64 path 1e-12 relative difference per step (sum-order rounding
 only), FP32 path 1e-5 per step (single-precision rounding of a handful of
@@ -43,6 +45,23 @@ def field_reldiff(a, b, n):
     return out
 
 
+def field_maxrel(a, b, n):
+    """max over the two fields of max_i |a_i - b_i| / max_i |b_i|: element by
+    element, so that a few wrong nodes (a boundary row, a tile edge) cannot
+    hide in a norm over millions of correct ones"""
+    out = 0.0
+    for s in (slice(0, n), slice(n, 2 * n)):
+        nb = np.abs(b[s]).max()
+        out = max(out, np.abs(a[s] - b[s]).max() / (nb if nb > 0 else 1.0))
+    return out
+
+
+def field_diff(a, b, n):
+    """both measures at once: a test's tolerance bounds the normwise and the
+    element-wise relative difference"""
+    return max(field_reldiff(a, b, n), field_maxrel(a, b, n))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs", "cgs"])
 @pytest.mark.parametrize("L", [2, 3, 5, 7, 9])
@@ -58,7 +77,7 @@ def test_smoother_step_parity(mg, oracle_mod, L, alpha, smoother, precision):
             s.smooth(dev(f), x, steps)
             got = host(x)
             want = o.smooth(f, x0, steps)
-            d = field_reldiff(got, want, n)
+            d = field_diff(got, want, n)
             assert d <= TOL[precision], (steps, d)
 
 
@@ -78,7 +97,7 @@ def test_smoothing_call_kernels(mg, oracle_mod, L, small_max, smoother, precisio
         for steps in (1, 2):
             x = dev(x0)
             s.smooth(dev(f), x, steps)
-            d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
+            d = field_diff(host(x), o.smooth(f, x0, steps), o.nn())
             assert d <= TOL[precision], (steps, d)
 
 
@@ -97,7 +116,7 @@ def test_cluster_smoothing_call(mg, oracle_mod, L, cs, smoother, precision):
         for steps in (1, 2):
             x = dev(x0)
             s.smooth(dev(f), x, steps)
-            d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
+            d = field_diff(host(x), o.smooth(f, x0, steps), o.nn())
             assert d <= TOL[precision], (steps, d)
 
 
@@ -114,7 +133,7 @@ def test_autotuned_kernels(mg, oracle_mod, smoother, precision):
     with mg.Solver(L, alpha, smoother=smoother, precision=precision, autotune=True) as s:
         x = dev(x0)
         s.smooth(dev(f), x, 2)
-        d = field_reldiff(host(x), o.smooth(f, x0, 2), o.nn())
+        d = field_diff(host(x), o.smooth(f, x0, 2), o.nn())
         assert d <= TOL[precision], d
         yD = inputs.yd_uniform(L, 0)
         fs = s.rhs_from_yd(dev(yD))
@@ -127,7 +146,7 @@ def test_autotuned_kernels(mg, oracle_mod, smoother, precision):
     with mg.Solver(L, alpha, smoother=smoother, precision=precision) as s:
         xd = torch.zeros_like(fs)
         s.solve(s.rhs_from_yd(dev(yD)), xd, tol=1e-10)
-    assert field_reldiff(host(xs), host(xd), o.nn()) <= 1e-8
+    assert field_diff(host(xs), host(xd), o.nn()) <= 1e-8
 
 
 @pytest.mark.parametrize("L,cs", [(8, 2), (7, 17), (6, 64)])
@@ -154,7 +173,7 @@ def test_lsgs_step_kernel_tiling(mg, oracle_mod, L, tile, precision):
         for steps in (1, 3):
             x = dev(x0)
             s.smooth(dev(f), x, steps)
-            d = field_reldiff(host(x), o.smooth(f, x0, steps), o.nn())
+            d = field_diff(host(x), o.smooth(f, x0, steps), o.nn())
             assert d <= TOL[precision], (steps, d)
 
 
@@ -170,10 +189,10 @@ def test_transfer_parity(mg, oracle_mod, L, precision):
     with mg.Solver(L, alpha, precision=precision) as s:
         fc = host(s.restrict(dev(f), dev(x)))
         want = o.restrict(o.residual(f, x))
-        assert field_reldiff(fc, want, nc) <= TOL[precision]
+        assert field_diff(fc, want, nc) <= TOL[precision]
         xg = dev(x)
         s.prolong_add(dev(xc), xg)
-        assert field_reldiff(host(xg), o.prolong_add(xc, x), n) <= TOL[precision]
+        assert field_diff(host(xg), o.prolong_add(xc, x), n) <= TOL[precision]
 
 
 @pytest.mark.parametrize("L", [1, 3, 6])
@@ -216,7 +235,7 @@ def test_cycle_parity_fp64(mg, oracle_mod, L, smoother, cycle, coarse_level):
         x = dev(x0)
         s.cycle(dev(f), x)
         want = o.cycle(f, x0)
-        assert field_reldiff(host(x), want, o.nn()) <= max(1e-12, 2.0 ** -52 * 4.0 ** L)
+        assert field_diff(host(x), want, o.nn()) <= max(1e-12, 2.0 ** -52 * 4.0 ** L)
 
 
 @pytest.mark.parametrize("coarse_level", [-1, 0])
@@ -242,7 +261,7 @@ def test_refinement_step_parity_fp32(mg, oracle_mod, L, smoother, coarse_level):
         d = o.cycle(r, np.zeros_like(r))
         want = x0 + d
         dg = host(x) - x0
-        assert field_reldiff(dg, d, o.nn()) <= max(1e-4, 2.0 ** -24 * 4.0 ** L)
+        assert field_diff(dg, d, o.nn()) <= max(1e-4, 2.0 ** -24 * 4.0 ** L)
 
 
 def solution_errors(o, x, xo):
