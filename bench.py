@@ -92,6 +92,8 @@ def parse():
     p.add_argument("--serial", action="store_true",
                    help="solve the alphas one after another instead of concurrently on separate streams")
     p.add_argument("--no-l12", action="store_true", help="skip the h = 2^-12 single-instance line")
+    p.add_argument("--no-batch256", action="store_true", help="skip the 256-instance batched-solve line")
+    p.add_argument("--no-autograd", action="store_true", help="skip the 16-instance differentiation line")
     p.add_argument("--profile-band", type=int, default=0, metavar="L",
                    help="for ncu captures: set up one FP32 LSGS handle at h = 2^-L and run --steps finest-level "
                         "smoothing steps (mg_smooth) after --warmup untimed ones; prints the CUDA-event time")
@@ -247,6 +249,9 @@ def run_ours(args, rank, world, local):
         fs = {a: s.rhs_from_yd(yD) for a, s in solvers.items()}
         xs = {a: torch.zeros_like(fs[a]) for a in solvers}
         its = {}
+        # all alphas in one graph-captured batch: one graph launch per step runs
+        # every solve to its own convergence (tests on the device)
+        batch = None if args.serial else mg.Batch([solvers[a] for a in ALPHAS])
         torch.cuda.synchronize()
 
         def one(a):
@@ -258,11 +263,9 @@ def run_ours(args, rank, world, local):
             if args.serial:
                 run_all(one)
                 return
-            # all alphas in flight at once through the library's batch call
             for a in ALPHAS:
                 xs[a].zero_()
-            it, rr, code = mg.solve_batch([solvers[a] for a in ALPHAS], [fs[a] for a in ALPHAS],
-                                          [xs[a] for a in ALPHAS], tol=args.tol)
+            it, rr, st, code = batch.solve([fs[a] for a in ALPHAS], [xs[a] for a in ALPHAS], tol=args.tol)
             for a, k in zip(ALPHAS, it):
                 its[a] = k
 
@@ -290,6 +293,8 @@ def run_ours(args, rank, world, local):
         ms = sum(a.elapsed_time(b) for a, b in ev)
         launches = sum(s.launches() for s in solvers.values()) - l0
         prof = [s.profile() for s in solvers.values()]
+        if batch is not None:
+            batch.close()
         return ms, its, launches, prof, clocks, xs
 
     def max_over_ranks(v):
@@ -361,6 +366,10 @@ def run_ours(args, rank, world, local):
 
     if not args.no_l12 and L == 11 and not args.profiling_run:
         out["l12"] = run_l12(args, mg, peak, pk is not None, flush)
+    if not args.no_batch256 and not args.profiling_run:
+        out["batch256"] = batch_line(args, 256, steps=2, warmup=1)
+    if not args.no_autograd and not args.profiling_run:
+        out["autograd16"] = run_autograd16(args)
 
     if not args.no_fp64:
         sol64 = make("fp64", False)
@@ -715,12 +724,13 @@ def run_protocol(args):
                       "seconds": time.time() - t0, "rows": rows}))
 
 
-def run_batch(args):
-    """The batched-solve configuration: independent instances with levels
-    uniform in 6..10, alpha log-uniform in [1e-8, 1], y_D ~ U(-1, 1) (one
-    generator, seed 2), LSGS W(2,2), FP32 cycles in FP64 refinement, all in
-    flight at once through mg_solve_batch; value = unknowns solved per second
-    over all instances (set-up excluded and reported)."""
+def batch_line(args, count, steps, warmup):
+    """The batched-solve configuration: `count` independent instances with
+    levels uniform in 6..10, alpha log-uniform in [1e-8, 1], y_D ~ U(-1, 1)
+    (one generator, seed 2), LSGS W(2,2), FP32 cycles in FP64 refinement, all
+    solved by one launch of a recorded batch graph (mg_batch_solve: the
+    convergence tests on the device); value = unknowns solved per second over
+    all instances (set-up and graph recording excluded and reported)."""
     import torch
 
     from paper_1502_03917_gb300 import build as B
@@ -728,12 +738,15 @@ def run_batch(args):
     import paper_1502_03917_gb300.aaomg as mg
 
     B.build()
-    levels, alphas, yds = inputs.batch_instances(args.batch, 2)
+    levels, alphas, yds = inputs.batch_instances(count, 2)
     t0 = time.time()
     solvers = [mg.Solver(L, a, smoother=args.smoother, precision="fp32_refine", cycle=args.cycle, max_iter=100,
                          inner_cycles=args.inner_cycles, autotune=args.autotune) for L, a in zip(levels, alphas)]
     torch.cuda.synchronize()
     setup_s = time.time() - t0
+    t0 = time.time()
+    batch = mg.Batch(solvers)
+    graph_s = time.time() - t0
     fs = [s.rhs_from_yd(torch.tensor(y, dtype=torch.float64, device="cuda")) for s, y in zip(solvers, yds)]
     xs = [torch.zeros_like(f) for f in fs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -741,13 +754,14 @@ def run_batch(args):
     def step():
         for x in xs:
             x.zero_()
-        return mg.solve_batch(solvers, fs, xs, tol=args.tol)
+        its, rrs, st, code = batch.solve(fs, xs, tol=args.tol)
+        return its, rrs, code
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    its = None
-    for k in range(args.steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    its = rrs = None
+    for k in range(steps):
         flush.fill_(float(k))
         ev[k][0].record()
         its, rrs, code = step()
@@ -758,13 +772,97 @@ def run_batch(args):
     hist = {}
     for k in its:
         hist[str(k)] = hist.get(str(k), 0) + 1
-    print(json.dumps({"metric": "batched solves: unknowns/s at %g rel. residual" % args.tol,
-                      "value": unknowns * args.steps / (ms / 1e3), "unit": UNIT, "instances": args.batch,
-                      "unknowns_per_step": unknowns, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": ms / args.steps, "setup_s": setup_s, "iterations": hist,
-                      "max_relres": max(rrs), "levels": {str(L): levels.count(L) for L in sorted(set(levels))},
-                      "config": "levels U{6..10}, log10 alpha ~ U[-8,0], y_D ~ U(-1,1), seed 2; "
-                                f"{args.smoother.upper()} {args.cycle}(2,2), FP32 cycles in FP64 refinement"}))
+    batch.close()
+    for s in solvers:
+        s.close()
+    return {"metric": "batched solves: unknowns/s at %g rel. residual" % args.tol,
+            "value": unknowns * steps / (ms / 1e3), "unit": UNIT, "instances": count,
+            "unknowns_per_step": unknowns, "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+            "setup_s": setup_s, "graph_s": graph_s, "iterations": hist, "max_relres": max(rrs),
+            "levels": {str(L): levels.count(L) for L in sorted(set(levels))},
+            "config": "levels U{6..10}, log10 alpha ~ U[-8,0], y_D ~ U(-1,1), seed 2; "
+                      f"{args.smoother.upper()} {args.cycle}(2,2), FP32 cycles in FP64 refinement, one batch graph "
+                      "launch per step, L2 flushed before each"}
+
+
+def run_batch(args):
+    print(json.dumps(batch_line(args, args.batch, args.steps, args.warmup)))
+
+
+def run_autograd16(args):
+    """The differentiation configuration: 16 instances at h = 2^-10, alpha =
+    1e-2, y_D ~ U(-1,1) (seed 4), u_target ~ N(0,1) (seed 3), loss
+    L = 1/2 sum_k ||u_k - u_target,k||^2 with u = lambda / alpha; one step = the
+    batched forward solve (FP32 + FP64 refinement, one batch graph) and the
+    batched adjoint solve (dL/dy_D and dL/dlog alpha).  Checked against central
+    finite differences (step 1e-6) of the same loss from FP64 solves, along a
+    random direction in y_D and in log alpha."""
+    import numpy as np
+    import torch
+
+    from paper_1502_03917_gb300.autograd import clear_cache, control
+
+    L, alpha, B = 10, 1e-2, 16
+    N = ((1 << L) + 1) ** 2
+    yD = torch.tensor(np.random.default_rng(4).uniform(-1.0, 1.0, (B, N)), dtype=torch.float64, device="cuda")
+    ut = torch.tensor(np.random.default_rng(3).standard_normal((B, N)), dtype=torch.float64, device="cuda")
+    tol = 1e-10
+
+    def grads():
+        y = yD.clone().requires_grad_(True)
+        la = torch.tensor(np.log(alpha), dtype=torch.float64, requires_grad=True)
+        u = control(y, la, L, tol=tol, precision="fp32_refine")
+        loss = 0.5 * ((u - ut) ** 2).sum()
+        loss.backward()
+        return y.grad, la.grad.item(), loss.item()
+
+    t0 = time.time()
+    grads()  # sets up (and caches) the 16 hierarchies and the batch graph
+    setup_s = time.time() - t0
+    K = 2
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        gy, gla, lval = grads()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+
+    # Finite-difference check of instance 0's loss L_0 = 1/2 ||u_0 - u_target,0||^2:
+    # its gradient through the same batched forward and adjoint solves (the
+    # other instances' adjoint right-hand sides are then zero), against central
+    # differences of FP64 solves of instance 0 alone.
+    import paper_1502_03917_gb300.aaomg as mg
+
+    y = yD.clone().requires_grad_(True)
+    la = torch.tensor(np.log(alpha), dtype=torch.float64, requires_grad=True)
+    u = control(y, la, L, tol=tol, precision="fp32_refine")
+    (0.5 * ((u[0] - ut[0]) ** 2).sum()).backward()
+    g0, gla0 = y.grad[0], la.grad.item()
+
+    def loss0(y0, a):
+        with mg.Solver(L, a, smoother="lsgs", precision="fp64", max_iter=200) as s:
+            f = s.rhs_from_yd(y0.contiguous())
+            x = torch.zeros_like(f)
+            s.solve(f, x, tol=1e-12, raise_on_fail=False)
+            return 0.5 * float(((s.control(x) - ut[0]) ** 2).sum())
+
+    h = 1e-6
+    v = torch.tensor(np.random.default_rng(8).standard_normal(N), dtype=torch.float64, device="cuda")
+    fd_y = (loss0(yD[0] + h * v, alpha) - loss0(yD[0] - h * v, alpha)) / (2 * h)
+    fd_a = (loss0(yD[0], alpha * np.exp(h)) - loss0(yD[0], alpha * np.exp(-h))) / (2 * h)
+    an_y = float((g0 * v).sum())
+    gla = gla0
+    clear_cache()
+    return {"metric": "gradients/s (dL/dy_D and dL/dlog alpha of 16 instances)", "value": B / (ms / 1e3),
+            "unit": "instance gradients/s", "instances": B, "level": L, "alpha": alpha,
+            "ms_per_step": ms, "steps": K, "setup_s": setup_s, "loss": lval,
+            "fd_check": {"instance": 0, "step": h, "precision": "fp64", "dLdv_adjoint": an_y, "dLdv_fd": fd_y,
+                         "rel_err_yD": abs(an_y - fd_y) / abs(fd_y), "dLdlogalpha_adjoint": gla,
+                         "dLdlogalpha_fd": fd_a, "rel_err_log_alpha": abs(gla - fd_a) / abs(fd_a)},
+            "config": "16 x h=2^-10, alpha=1e-2, y_D ~ U(-1,1) seed 4, u_target ~ N(0,1) seed 3, LSGS W(2,2), "
+                      "FP32+FP64-refine forward and adjoint solves to 1e-10, one batch graph each"}
 
 
 def main():

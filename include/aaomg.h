@@ -159,17 +159,71 @@ AAOMG_API int mg_cycle(mg_handle h, const double* f, double* x, void* stream);
  * NaN or blow-up.  Device pointers. */
 AAOMG_API int mg_solve(mg_handle h, const double* f, double* x, double tol, int* iters, double* relres, void* stream);
 
+/* The iteration count of section 3's protocol on the finest level: zero
+ * right-hand side, initial iterate x0 (2N doubles, device, not modified), one
+ * iteration (mg_cycle) at a time until the error ||x||_L (the exact solution
+ * is 0) has dropped below reduction * ||x0||_L, with L = diag(Q) of section 2.
+ * *iters receives the count, or -1 (status NOT_CONVERGED) if max_iter
+ * iterations do not reach it, or -1 (DIVERGED) on a non-finite norm.
+ * mg_get_history then gives ||x_k||_L / ||x0||_L.  Synchronises `stream` once
+ * per iteration (the test is on the host). */
+AAOMG_API int mg_protocol_iterations(mg_handle h, const double* x0, double reduction, int max_iter, int* iters,
+                                     void* stream);
+
 /* mg_solve with f and x in HOST memory (pinned or pageable): copies f and x to
  * the device, solves, and copies x back, all on `stream`. */
 AAOMG_API int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol, int* iters, double* relres,
                   void* stream);
 
-/* Independent problems in one call: handles[k] solves A_k x_k = f_k from the
- * initial guess in x_k (device pointers) to `tol`, all instances in flight at
- * once (each on a stream of its own handle, ordered after the work already on
- * `stream`; `stream` waits for all of them).  iters / relres (NULL or arrays of
- * count) receive each instance's result.  The handles must be distinct.
- * Returns the first nonzero status of an instance, else AAOMG_OK. */
+/* Batched solves of independent problems (many right-hand sides, values of
+ * alpha and grid sizes; the paper solves one problem at a time).
+ *
+ * mg_batch_create records ONE CUDA graph over `count` distinct handles (all on
+ * the current device, none with opt.profile = 1): one branch per instance,
+ * made of the residual norms of the initial iterate, a convergence test, and a
+ * conditional while node whose body is one iteration of that handle (its
+ * cycle, or its FP32 cycles and FP64 refinement update), the new residual norms
+ * and the test again.  The tests run on the device (the same decisions as
+ * mg_solve: diverged, converged to tol, max_iter reached), so one launch of the
+ * graph takes every instance to its own convergence with no host round trip;
+ * the branches are independent, so the GPU runs the instances' kernels
+ * concurrently.  The batch keeps pointers to the handles: they must outlive it,
+ * and a handle must not be used by another call while a batch solve runs.
+ * Errors: BAD_ARG (null, repeated, profiled or multi-device handles), OOM, CUDA.
+ */
+typedef struct mg_batch_ctx* mg_batch;
+AAOMG_API int mg_batch_create(int count, const mg_handle* handles, mg_batch* out);
+
+/* Solve handles[k] A_k x_k = f_k from the initial guesses x_k to `tol` for
+ * every k (f, x: arrays of `count` device pointers, 2N_k doubles each; x is
+ * in/out): copies f_k and x_k into the handles, launches the batch graph on
+ * `stream`, copies the solutions back and synchronises.  iters, relres and
+ * status (NULL or arrays of count) receive each instance's iteration count,
+ * final relative residual and status; mg_get_history of each handle gives its
+ * residual history.  Returns the first nonzero instance status, else AAOMG_OK. */
+AAOMG_API int mg_batch_solve(mg_batch b, const double* const* f, double* const* x, double tol, int* iters,
+                             double* relres, int* status, void* stream);
+
+/* Batched adjoint of the solves (mg_adjoint for every instance at once): given
+ * each instance's solution x_k of A_k x_k = (M y_D,k, 0) and ubar_k = dL/du_k
+ * (N_k doubles), solves A_k z_k = (0, ubar_k / alpha_k) from zero to `tol` in
+ * one launch of the batch graph and returns gyD_k = dL/dy_D,k = M z_k,y
+ * (N_k doubles) and dalpha[k] = -alpha_k^{-2} (ubar_k . lambda_k +
+ * z_k,lambda^T M lambda_k) (host array of count; eq. (mp2), dA/dalpha =
+ * [[0,0],[0,alpha^{-2} M]]).  x, ubar, z (2N_k doubles, receives the adjoint
+ * state), gyD: arrays of count device pointers.  iters (NULL or count ints)
+ * receives the adjoint iteration counts.  Returns the first nonzero instance
+ * status, else AAOMG_OK. */
+AAOMG_API int mg_batch_adjoint(mg_batch b, const double* const* x, const double* const* ubar, double* const* z,
+                               double* const* gyD, double* dalpha, double tol, int* iters, void* stream);
+
+/* Free a batch (NULL is ignored); the handles stay valid.  Synchronises the device. */
+AAOMG_API void mg_batch_destroy(mg_batch b);
+
+/* One-shot batch: mg_batch_create, mg_batch_solve and mg_batch_destroy in one
+ * call (the graph is recorded and instantiated each time; keep an mg_batch for
+ * repeated solves).  Returns the first nonzero status of an instance, else
+ * AAOMG_OK. */
 AAOMG_API int mg_solve_batch(int count, const mg_handle* handles, const double* const* f, double* const* x, double tol,
                              int* iters, double* relres, void* stream);
 

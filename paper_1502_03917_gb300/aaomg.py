@@ -85,6 +85,7 @@ def load():
             "mg_cycle": (I, [H, P, P, P]),
             "mg_solve": (I, [H, P, P, D, pI, pD, P]),
             "mg_solve_host": (I, [H, P, P, D, pI, pD, P]),
+            "mg_protocol_iterations": (I, [H, P, D, I, pI, P]),
             "mg_get_history": (I, [H, pD, I, pI]),
             "mg_norms": (I, [H, P, pD, pD, P]),
             "mg_level_kernel": (I, [H, I, pI, pI]),
@@ -93,6 +94,11 @@ def load():
             "mg_reset_profile": (I, [H]),
             "mg_residual_noalloc": (I, [I, D, I, P, P, P, pD, P]),
             "mg_solve_batch": (I, [I, ctypes.POINTER(H), ctypes.POINTER(P), ctypes.POINTER(P), D, pI, pD, P]),
+            "mg_batch_create": (I, [I, ctypes.POINTER(H), ctypes.POINTER(H)]),
+            "mg_batch_solve": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), D, pI, pD, pI, P]),
+            "mg_batch_destroy": (None, [H]),
+            "mg_batch_adjoint": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                     pD, D, pI, P]),
             "mg_control": (I, [H, P, P, P]),
             "mg_adjoint": (I, [H, P, P, P, P, pD, D, P]),
             "mg_strerror": (ctypes.c_char_p, [I]),
@@ -146,9 +152,74 @@ def residual_noalloc(levels: int, alpha: float, f, x, r=None, k_variant: int = 0
     return rr.value
 
 
+class Batch:
+    """One graph-captured batch over several solvers (mg_batch_create): every
+    solve() launches a single CUDA graph that runs each instance to its own
+    convergence, the tests on the device.  The solvers must stay open while
+    the batch is used."""
+
+    def __init__(self, solvers):
+        self._lib = load()
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        hs = (ctypes.c_void_p * n)(*[s._h for s in self.solvers])
+        b = ctypes.c_void_p()
+        _check(self._lib.mg_batch_create(n, hs, ctypes.byref(b)), "mg_batch_create")
+        self._b = b
+
+    def solve(self, fs, xs, tol: float = 1e-8, raise_on_fail: bool = True):
+        """Solve solvers[k] on (fs[k], xs[k]) for all k (xs in/out); returns
+        (iterations, relative residuals, per-instance status, first status)."""
+        n = len(self.solvers)
+        fp = (ctypes.c_void_p * n)(*[_dptr(f, 2 * s.N) for s, f in zip(self.solvers, fs)])
+        xp = (ctypes.c_void_p * n)(*[_dptr(x, 2 * s.N) for s, x in zip(self.solvers, xs)])
+        it = (ctypes.c_int * n)()
+        rr = (ctypes.c_double * n)()
+        st = (ctypes.c_int * n)()
+        code = self._lib.mg_batch_solve(self._b, fp, xp, float(tol), it, rr, st, _stream())
+        if raise_on_fail:
+            _check(code, "mg_batch_solve")
+        return list(it), list(rr), list(st), code
+
+    def adjoint(self, xs, ubars, tol: float = 1e-10):
+        """Batched mg_adjoint: for every instance the adjoint solve of the loss
+        gradient ubars[k] = dL/du_k at the solution xs[k]; returns (gyD list,
+        dL/dalpha list, z list, adjoint iterations)."""
+        import torch
+
+        n = len(self.solvers)
+        zs = [torch.empty(2 * s.N, dtype=torch.float64, device=x.device) for s, x in zip(self.solvers, xs)]
+        gs = [torch.empty(s.N, dtype=torch.float64, device=x.device) for s, x in zip(self.solvers, xs)]
+        arr = lambda ts, m: (ctypes.c_void_p * n)(*[_dptr(t, m(s)) for s, t in zip(self.solvers, ts)])  # noqa: E731
+        da = (ctypes.c_double * n)()
+        it = (ctypes.c_int * n)()
+        _check(self._lib.mg_batch_adjoint(self._b, arr(xs, lambda s: 2 * s.N), arr(ubars, lambda s: s.N),
+                                          arr(zs, lambda s: 2 * s.N), arr(gs, lambda s: s.N), da, float(tol), it,
+                                          _stream()), "mg_batch_adjoint")
+        return gs, list(da), zs, list(it)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.mg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 def solve_batch(solvers, fs, xs, tol: float = 1e-8, raise_on_fail: bool = True):
-    """Solve independent problems at once (mg_solve_batch): solvers[k] on
-    (fs[k], xs[k]); returns (iterations, relative residuals, status)."""
+    """Solve independent problems at once (mg_solve_batch: a one-shot batch
+    graph): solvers[k] on (fs[k], xs[k]); returns (iterations, relative
+    residuals, status)."""
     lib = load()
     n = len(solvers)
     hs = (ctypes.c_void_p * n)(*[s._h for s in solvers])
@@ -264,20 +335,14 @@ class Solver:
         return a.value, b.value
 
     def protocol_iterations(self, x0, reduction: float = 1e-6, max_iter: int = 300) -> int:
-        """Section 3's protocol: zero right-hand side, start x0 (not modified),
-        cycles until ||x||_L has dropped by `reduction`; -1 if max_iter is hit."""
-        import torch
-
-        x = x0.clone()
-        f = torch.zeros_like(x)
-        e0 = self.norms(x)[0]
-        it = 0
-        while self.norms(x)[0] > reduction * e0:
-            if it >= max_iter:
-                return -1
-            self.cycle(f, x)
-            it += 1
-        return it
+        """Section 3's protocol (mg_protocol_iterations): zero right-hand side,
+        start x0 (not modified), cycles until ||x||_L has dropped by
+        `reduction`; -1 if max_iter is hit."""
+        it = ctypes.c_int()
+        code = self._lib.mg_protocol_iterations(self._h, _dptr(x0, 2 * self.N), float(reduction), int(max_iter),
+                                                ctypes.byref(it), _stream())
+        _check(code, "mg_protocol_iterations", allow=(ERR_NOT_CONVERGED,))
+        return it.value
 
     def solve_host(self, f, x, tol: float = 1e-8, raise_on_fail: bool = True):
         """f, x: C-contiguous float64 numpy arrays (x in/out) in host memory."""

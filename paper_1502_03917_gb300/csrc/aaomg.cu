@@ -4,6 +4,7 @@
 // declared in include/aaomg.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,7 +17,9 @@
 #include "coarse.h"
 #include "common.cuh"
 #include "launch.h"
+#include "pdl.h"
 #include "strips.h"
+#include "trace.h"
 
 using namespace aaomg;
 
@@ -240,7 +243,69 @@ struct mg_ctx {
     long long prof_sweeps = 0, sweeps_per_iter = 0;
 };
 
+// State of one instance of a graph-captured batch solve (device memory).
+struct BatchState {
+    int it;      // iterations run
+    int status;  // AAOMG_OK, NOT_CONVERGED or DIVERGED once the instance has stopped
+    double rr;   // relative residual ||f - A x||_{L^-1} / ||f||_{L^-1} of the current iterate
+    double r0;   // the initial one
+};
+
+struct mg_batch_ctx {
+    int count = 0;
+    int dev = 0;
+    std::vector<mg_ctx*> H;
+    std::vector<long long> body_kernels;  // kernels of one iteration of each instance
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    BatchState* d_state = nullptr;
+    BatchState* h_state = nullptr;
+    double* d_hist = nullptr;  // count x hcap residual histories
+    double* h_hist = nullptr;
+    int hcap = 0;
+    double* d_tol = nullptr;
+    double* h_tol = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+};
+
 namespace {
+
+// The convergence test of the solve loop, on the device: reads the norms that
+// the preceding residual kernels left in red, records the relative residual,
+// decides as the host loop does (diverged, converged to tol, out of
+// iterations, else one more iteration) and sets the condition of the
+// instance's while node.  first: the test of the initial residual.
+__global__ void k_batch_check(const double* __restrict__ red, BatchState* st, double* hist, int hcap,
+                              const double* __restrict__ tol, int max_iter, cudaGraphConditionalHandle h, int first) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double fn = red[1] > 0.0 ? red[1] : 1.0;
+    const double rr = sqrt(red[0] / fn);
+    BatchState b;
+    if (first) {
+        b.it = 0;
+        b.status = AAOMG_OK;
+        b.r0 = rr;
+    } else {
+        b = *st;
+    }
+    if (b.it < hcap) hist[b.it] = rr;
+    b.rr = rr;
+    unsigned go = 0;
+    if (!isfinite(rr) || rr > 1e6 * (b.r0 > 0.0 ? b.r0 : 1.0)) {
+        b.status = AAOMG_ERR_DIVERGED;
+    } else if (rr <= *tol) {
+        b.status = AAOMG_OK;
+    } else if (b.it >= max_iter) {
+        b.status = AAOMG_ERR_NOT_CONVERGED;
+    } else {
+        go = 1;
+        b.it += 1;
+    }
+    *st = b;
+    cudaGraphSetConditional(h, go);
+}
 
 template <>
 const CtaParams<float>& ctap<float>(const mg_ctx* H) {
@@ -281,9 +346,20 @@ int dalloc(mg_ctx* H, void** p, size_t bytes) {
 
 // ------------------------------------------------------------ the cycle --
 
+const char* smoother_name(int sm) {
+    switch (sm) {
+    case MG_SMOOTHER_NE: return "NE";
+    case MG_SMOOTHER_LSGS: return "LSGS";
+    case MG_SMOOTHER_SLSGS: return "sLSGS";
+    case MG_SMOOTHER_CGS: return "CGS";
+    default: return "?";
+    }
+}
+
 template <typename T>
 void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     if (steps <= 0) return;
+    TraceRange tr("level %d: %d %s steps", l, steps, smoother_name(H->o.smoother));
     Lev& v = H->lev[l];
     const LevelP<T>& P = lp<T>(v);
     T* x = (T*)v.x;
@@ -365,6 +441,7 @@ template <typename T>
 void cycle(mg_ctx* H, int l, int count, cudaStream_t s) {
     Lev& v = H->lev[l];
     const LevelP<T>& P = lp<T>(v);
+    TraceRange tr("level %d: %d cycle(s)", l, count);
     if (l <= H->lc) {
         launch_coarse_cycle<T>(ctap<T>(H), (const T*)v.f, (T*)v.x, H->ainv, count, s);
         H->rec_kernels += 1;
@@ -452,6 +529,7 @@ int build_class_table(mg_ctx* H, Lev& v, double km) {
 // steps, once to warm up and then three times under CUDA events.
 template <typename T>
 int autotune_levels(mg_ctx* H, double km) {
+    TraceRange tr("autotune level kernels");
     cudaStream_t s = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -513,6 +591,7 @@ int default_cluster(int n, bool fp32) {
 // by the single-block kernel, one block per unit vector, in the cycles'
 // precision and with the operator scaled as the cycles use it.
 int build_dense_coarse(mg_ctx* H, double km) {
+    TraceRange tr("dense map of level %d", H->ld);
     int ld = H->ld;
     int64_t m = 2 * (int64_t)((1 << ld) + 1) * ((1 << ld) + 1);
     H->bm = (int)m;
@@ -546,6 +625,7 @@ int build_dense_coarse(mg_ctx* H, double km) {
 }
 
 int build_graph(mg_ctx* H) {
+    TraceRange tr("record iteration graph");
     CK(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
     if (H->o.profile) {
         // two smoothing calls per visit of the profiled level; a cycle visits
@@ -592,6 +672,7 @@ int collect_profile(mg_ctx* H) {
 }
 
 int run_iteration(mg_ctx* H, cudaStream_t s) {
+    TraceRange tr("iteration (graph launch)");
     CK(cudaGraphLaunch(H->gexec, s));
     H->launches += H->graph_kernels;
     if (H->o.profile) H->pending = true;
@@ -658,6 +739,7 @@ int solve_step(mg_ctx* H, double tol, SolveState& st, cudaStream_t s) {
 }
 
 int solve_internal(mg_ctx* H, double tol, int* iters, double* relres, cudaStream_t s) {
+    TraceRange tr("solve L=%d alpha=%g %s", H->L, H->alpha, H->fp32 ? "fp32+refine" : "fp64");
     SolveState st;
     int rc = solve_begin(H, s);
     if (rc) return rc;
@@ -670,6 +752,103 @@ int solve_internal(mg_ctx* H, double tol, int* iters, double* relres, cudaStream
     if (iters) *iters = st.it;
     if (relres) *relres = st.rr;
     return st.status;
+}
+
+// The residual and its norms on the device only (no copy to the host): the
+// FP64 defect of the iterate, its dual norm and that of f into H->red, and
+// for FP32 cycles the scaled FP32 defect on the finest level.
+int queue_norms_dev(mg_ctx* H, cudaStream_t s) {
+    Lev& v = H->lev[H->L];
+    float* fin = H->fp32 ? (float*)v.f : nullptr;
+    launch_resid64(H->fine64, iter_f(H), iter_x(H), nullptr, fin, v.ld, v.fs, H->part, kResidBlocks, H->red, s);
+    CK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+// Record the batch graph: one branch per instance, each
+//   residual norms of the initial iterate -> test -> while (test passed) {
+//     one iteration (the handle's cycle or refinement step) -> norms -> test }
+// so that a launch of the graph runs every instance to its own convergence
+// with no host round trip.  The kernels of one iteration are those of the
+// handle's own graph (record_iteration), recorded again into the while body.
+int batch_record(mg_batch_ctx* B, bool pdl_off) {
+    TraceRange tr("record batch graph (%d instances)", B->count);
+    int rc = AAOMG_OK;
+    g_pdl_off = pdl_off;
+    std::vector<cudaStream_t> capturing;  // streams whose capture must be ended on failure
+    auto bail = [&](int code, const std::string& msg) {
+        for (cudaStream_t cs : capturing) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        g_pdl_off = false;
+        return fail(code, msg);
+    };
+#define BCK(call)                                                                                           \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) return bail(AAOMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+    BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+    capturing.push_back(B->cap);
+    BCK(cudaEventRecord(B->fork, B->cap));
+    for (int k = 0; k < B->count && !rc; ++k) {
+        mg_ctx* H = B->H[k];
+        cudaStream_t s = H->own;
+        BCK(cudaStreamWaitEvent(s, B->fork, 0));
+        if ((rc = queue_norms_dev(H, s))) return bail(rc, g_err);
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edata = nullptr;
+        size_t nd = 0;
+        BCK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edata, &nd));
+        cudaGraphConditionalHandle ch;
+        BCK(cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
+        k_batch_check<<<1, 32, 0, s>>>(H->red, B->d_state + k, B->d_hist + (size_t)k * B->hcap, B->hcap, B->d_tol,
+                                        H->o.max_iter, ch, 1);
+        BCK(cudaGetLastError());
+        BCK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edata, &nd));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = ch;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        BCK(cudaGraphAddNode(&wnode, g, deps, edata, nd, &np));
+        BCK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        BCK(cudaStreamBeginCaptureToGraph(H->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        capturing.push_back(H->cap);
+        H->rec_kernels = 0;
+        if ((rc = record_iteration(H, H->cap)) || (rc = queue_norms_dev(H, H->cap))) return bail(rc, g_err);
+        B->body_kernels[k] = H->rec_kernels + 3;
+        k_batch_check<<<1, 32, 0, H->cap>>>(H->red, B->d_state + k, B->d_hist + (size_t)k * B->hcap, B->hcap,
+                                             B->d_tol, H->o.max_iter, ch, 0);
+        BCK(cudaGetLastError());
+        cudaGraph_t done = nullptr;
+        capturing.pop_back();
+        BCK(cudaStreamEndCapture(H->cap, &done));
+        BCK(cudaEventRecord(B->join[k], s));
+        BCK(cudaStreamWaitEvent(B->cap, B->join[k], 0));
+    }
+    capturing.clear();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+    g_pdl_off = false;
+    if (e != cudaSuccess) return fail(AAOMG_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&B->gexec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        B->gexec = nullptr;
+        return fail(AAOMG_ERR_CUDA, std::string("batch graph instantiation: ") + cudaGetErrorString(e));
+    }
+    B->graph = g;
+#undef BCK
+    return AAOMG_OK;
 }
 
 // copy the caller's (FP64, paper's scaling) vector into the FP32 finest level
@@ -713,6 +892,7 @@ void mg_destroy(mg_handle h) {
 }
 
 int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
+    TraceRange tr("mg_setup L=%d alpha=%g", levels, alpha);
     if (!out) return fail(AAOMG_ERR_BAD_ARG, "out is null");
     *out = nullptr;
     if (levels < 1 || levels > AAOMG_MAX_LEVELS) return fail(AAOMG_ERR_BAD_ARG, "levels must be in [1, 13]");
@@ -796,7 +976,8 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
             break;
         CK(cudaMemset(v.x, 0, bytes));
         CK(cudaMemset(v.x2, 0, bytes));
-        v.bg = H->fp32 ? band_grid<float>(v.n, o.tile_w, o.tile_h, H->nsm) : band_grid<double>(v.n, o.tile_w, o.tile_h, H->nsm);
+        v.bg = H->fp32 ? band_grid<float>(v.n, o.tile_w, o.tile_h, H->nsm * band_blocks_per_sm<float>())
+                       : band_grid<double>(v.n, o.tile_w, o.tile_h, H->nsm * band_blocks_per_sm<double>());
         v.band = v.n + 1 >= H->band_min;
         CK(cudaMemset(v.f, 0, bytes));
         CK(cudaMemset(v.rh, 0, bytes));
@@ -1080,6 +1261,55 @@ int mg_solve(mg_handle h, const double* f, double* x, double tol, int* iters, do
     return status;
 }
 
+int mg_protocol_iterations(mg_handle h, const double* x0, double reduction, int max_iter, int* iters, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x0 || !iters || !(reduction > 0.0) || max_iter < 0)
+        return fail(AAOMG_ERR_BAD_ARG, "null vector or output, reduction <= 0 or max_iter < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = (size_t)vec_bytes(h);
+    // zero right-hand side, the random start as the iterate
+    CK(cudaMemsetAsync(iter_f(h), 0, bytes, s));
+    CK(cudaMemcpyAsync(iter_x(h), x0, bytes, cudaMemcpyDeviceToDevice, s));
+    auto norm_L = [&](double& out) -> int {
+        launch_norms64(h->fine64, iter_x(h), h->part, kResidBlocks, h->red, s);
+        h->launches += 2;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h->h_red, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        out = std::sqrt(h->h_red[0]);
+        return AAOMG_OK;
+    };
+    double e0 = 0.0, e = 0.0;
+    if ((rc = norm_L(e0))) return rc;
+    e = e0;
+    int it = 0;
+    h->hist.assign(1, 1.0);
+    while (e > reduction * e0) {
+        if (it >= max_iter) {
+            *iters = -1;
+            return fail(AAOMG_ERR_NOT_CONVERGED, "protocol: max_iter reached");
+        }
+        if (h->fp32) {
+            // the refinement step's FP64 defect (f = 0) as the FP32 cycles' right-hand side
+            Lev& v = h->lev[h->L];
+            launch_resid64(h->fine64, iter_f(h), iter_x(h), nullptr, (float*)v.f, v.ld, v.fs, h->part, kResidBlocks,
+                           h->red, s);
+            h->launches += 2;
+        }
+        if ((rc = run_iteration(h, s))) return rc;
+        ++it;
+        if ((rc = norm_L(e))) return rc;
+        h->hist.push_back(e0 > 0.0 ? e / e0 : 0.0);
+        if (!std::isfinite(e)) {
+            *iters = -1;
+            return fail(AAOMG_ERR_DIVERGED, "protocol: the error norm is not finite");
+        }
+    }
+    *iters = it;
+    return AAOMG_OK;
+}
+
 int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol, int* iters, double* relres,
                   void* stream) {
     int rc = check_handle(h);
@@ -1096,55 +1326,178 @@ int mg_solve_host(mg_handle h, const double* f_host, double* x_host, double tol,
     return status;
 }
 
+void mg_batch_destroy(mg_batch b) {
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->d_state) cudaFree(b->d_state);
+    if (b->d_hist) cudaFree(b->d_hist);
+    if (b->d_tol) cudaFree(b->d_tol);
+    if (b->h_state) cudaFreeHost(b->h_state);
+    if (b->h_hist) cudaFreeHost(b->h_hist);
+    if (b->h_tol) cudaFreeHost(b->h_tol);
+    delete b;
+}
+
+int mg_batch_create(int count, const mg_handle* handles, mg_batch* out) {
+    if (!out) return fail(AAOMG_ERR_BAD_ARG, "out is null");
+    *out = nullptr;
+    if (count < 1 || !handles) return fail(AAOMG_ERR_BAD_ARG, "a batch needs at least one handle");
+    for (int k = 0; k < count; ++k) {
+        if (!handles[k]) return fail(AAOMG_ERR_BAD_ARG, "null handle in batch");
+        if (handles[k]->dev != handles[0]->dev) return fail(AAOMG_ERR_BAD_ARG, "the handles of a batch are on different devices");
+        if (handles[k]->o.profile) return fail(AAOMG_ERR_BAD_ARG, "a profiled handle (profile = 1) cannot be batched");
+        for (int q = 0; q < k; ++q)
+            if (handles[q] == handles[k]) return fail(AAOMG_ERR_BAD_ARG, "a handle appears twice in the batch");
+    }
+    int rc = check_handle(handles[0]);
+    if (rc) return rc;
+    mg_batch_ctx* B = new (std::nothrow) mg_batch_ctx();
+    if (!B) return fail(AAOMG_ERR_OOM, "host allocation");
+    B->count = count;
+    B->dev = handles[0]->dev;
+    B->H.assign(handles, handles + count);
+    B->body_kernels.assign(count, 0);
+    B->join.assign(count, nullptr);
+    for (int k = 0; k < count; ++k) B->hcap = std::max(B->hcap, handles[k]->o.max_iter + 1);
+    auto cleanup = [&](int code) {
+        mg_batch_destroy(B);
+        return code;
+    };
+    cudaError_t e = cudaMalloc((void**)&B->d_state, sizeof(BatchState) * count);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_hist, sizeof(double) * (size_t)count * B->hcap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_tol, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_state, sizeof(BatchState) * count);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_hist, sizeof(double) * (size_t)count * B->hcap);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->h_tol, sizeof(double));
+    if (e != cudaSuccess)
+        return cleanup(fail(e == cudaErrorMemoryAllocation ? AAOMG_ERR_OOM : AAOMG_ERR_CUDA,
+                            std::string("batch buffers: ") + cudaGetErrorString(e)));
+    e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&B->join[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cleanup(fail(AAOMG_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e)));
+    // programmatic edges inside the while bodies where the driver accepts
+    // them, else plain serialisation
+    rc = batch_record(B, false);
+    if (rc == AAOMG_ERR_CUDA) rc = batch_record(B, true);
+    if (rc) return cleanup(rc);
+    *out = B;
+    return AAOMG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Launch the batch graph on s with the tolerance tol (the instances' f and x
+// already set).
+int batch_launch(mg_batch b, double tol, cudaStream_t s) {
+    TraceRange tr("batch graph launch (%d instances)", b->count);
+    *b->h_tol = tol;
+    CK(cudaMemcpyAsync(b->d_tol, b->h_tol, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaGraphLaunch(b->gexec, s));
+    return AAOMG_OK;
+}
+
+// Read the instances' states and residual histories after the work queued on
+// s, fill the outputs (each may be NULL) and return the first nonzero status.
+int batch_finish(mg_batch b, cudaStream_t s, int* iters, double* relres, int* status) {
+    CK(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(BatchState) * b->count, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b->h_hist, b->d_hist, sizeof(double) * (size_t)b->count * b->hcap, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int first = AAOMG_OK;
+    for (int k = 0; k < b->count; ++k) {
+        mg_ctx* H = b->H[k];
+        const BatchState& st = b->h_state[k];
+        const int nh = std::min(st.it + 1, b->hcap);
+        H->hist.assign(b->h_hist + (size_t)k * b->hcap, b->h_hist + (size_t)k * b->hcap + nh);
+        H->launches += 3 + (long long)st.it * b->body_kernels[k];
+        if (iters) iters[k] = st.it;
+        if (relres) relres[k] = st.rr;
+        if (status) status[k] = st.status;
+        if (st.status != AAOMG_OK && first == AAOMG_OK) first = st.status;
+    }
+    if (first == AAOMG_ERR_NOT_CONVERGED) g_err = "max_iter reached";
+    else if (first == AAOMG_ERR_DIVERGED) g_err = "residual diverged";
+    return first;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_batch_solve(mg_batch b, const double* const* f, double* const* x, double tol, int* iters, double* relres,
+                   int* status, void* stream) {
+    if (!b || !f || !x || !(tol >= 0.0)) return fail(AAOMG_ERR_BAD_ARG, "bad batch arguments");
+    for (int k = 0; k < b->count; ++k)
+        if (!f[k] || !x[k]) return fail(AAOMG_ERR_BAD_ARG, "null vector in batch");
+    int rc = check_handle(b->H[0]);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < b->count; ++k) {
+        mg_ctx* H = b->H[k];
+        size_t bytes = (size_t)vec_bytes(H);
+        CK(cudaMemcpyAsync(iter_f(H), f[k], bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(iter_x(H), x[k], bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    if ((rc = batch_launch(b, tol, s))) return rc;
+    for (int k = 0; k < b->count; ++k)
+        CK(cudaMemcpyAsync(x[k], iter_x(b->H[k]), (size_t)vec_bytes(b->H[k]), cudaMemcpyDeviceToDevice, s));
+    return batch_finish(b, s, iters, relres, status);
+}
+
+int mg_batch_adjoint(mg_batch b, const double* const* x, const double* const* ubar, double* const* z,
+                     double* const* gyD, double* dalpha, double tol, int* iters, void* stream) {
+    if (!b || !x || !ubar || !z || !gyD || !dalpha || !(tol >= 0.0)) return fail(AAOMG_ERR_BAD_ARG, "bad batch arguments");
+    for (int k = 0; k < b->count; ++k)
+        if (!x[k] || !ubar[k] || !z[k] || !gyD[k]) return fail(AAOMG_ERR_BAD_ARG, "null vector in batch");
+    int rc = check_handle(b->H[0]);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // adjoint right-hand sides (0, ubar / alpha) into the handles, z from zero
+    for (int k = 0; k < b->count; ++k) {
+        mg_ctx* H = b->H[k];
+        launch_adjoint_rhs(H->fine64.fs, ubar[k], H->alpha, iter_f(H), s);
+        CK(cudaMemsetAsync(iter_x(H), 0, (size_t)vec_bytes(H), s));
+        H->launches += 1;
+    }
+    if ((rc = batch_launch(b, tol, s))) return rc;
+    for (int k = 0; k < b->count; ++k) {
+        mg_ctx* H = b->H[k];
+        CK(cudaMemcpyAsync(z[k], iter_x(H), (size_t)vec_bytes(H), cudaMemcpyDeviceToDevice, s));
+        launch_adjoint_terms(H->fine64, x[k], ubar[k], z[k], gyD[k], H->part, kResidBlocks, H->red, s);
+        H->launches += 2;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(H->h_red, H->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    rc = batch_finish(b, s, iters, nullptr, nullptr);
+    for (int k = 0; k < b->count; ++k) {
+        const mg_ctx* H = b->H[k];
+        dalpha[k] = -(H->h_red[0] + H->h_red[1]) / (H->alpha * H->alpha);
+    }
+    return rc;
+}
+
 int mg_solve_batch(int count, const mg_handle* handles, const double* const* f, double* const* x, double tol,
                    int* iters, double* relres, void* stream) {
     if (count < 0 || (count > 0 && (!handles || !f || !x)) || !(tol >= 0.0))
         return fail(AAOMG_ERR_BAD_ARG, "bad batch arguments");
-    for (int k = 0; k < count; ++k) {
-        if (!handles[k] || !f[k] || !x[k]) return fail(AAOMG_ERR_BAD_ARG, "null handle or vector in batch");
-        for (int q = 0; q < k; ++q)
-            if (handles[q] == handles[k]) return fail(AAOMG_ERR_BAD_ARG, "a handle appears twice in the batch");
-    }
     if (count == 0) return AAOMG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    int rc = check_handle(handles[0]);
+    mg_batch b = nullptr;
+    int rc = mg_batch_create(count, handles, &b);
     if (rc) return rc;
-    cudaEvent_t start = nullptr;
-    CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    CK(cudaEventRecord(start, s));
-    std::vector<SolveState> st(count);
-    std::vector<char> active(count, 1);
-    int status = AAOMG_OK;
-    for (int k = 0; k < count; ++k) {
-        mg_ctx* H = handles[k];
-        size_t bytes = (size_t)vec_bytes(H);
-        CK(cudaStreamWaitEvent(H->own, start, 0));
-        CK(cudaMemcpyAsync(iter_f(H), f[k], bytes, cudaMemcpyDeviceToDevice, H->own));
-        CK(cudaMemcpyAsync(iter_x(H), x[k], bytes, cudaMemcpyDeviceToDevice, H->own));
-        if ((rc = solve_begin(H, H->own))) return rc;
-    }
-    int left = count;
-    while (left > 0) {
-        for (int k = 0; k < count; ++k) {
-            if (!active[k]) continue;
-            mg_ctx* H = handles[k];
-            CK(cudaEventSynchronize(H->norms_ready));
-            rc = solve_step(H, tol, st[k], H->own);
-            if (rc < 0) return rc;
-            if (rc == 1) {
-                active[k] = 0;
-                --left;
-                CK(cudaMemcpyAsync(x[k], iter_x(H), (size_t)vec_bytes(H), cudaMemcpyDeviceToDevice, H->own));
-                CK(cudaEventRecord(H->norms_ready, H->own));
-                CK(cudaStreamWaitEvent(s, H->norms_ready, 0));
-                if (iters) iters[k] = st[k].it;
-                if (relres) relres[k] = st[k].rr;
-                if (st[k].status != AAOMG_OK && status == AAOMG_OK) status = st[k].status;
-            }
-        }
-    }
-    cudaEventDestroy(start);
-    return status;
+    rc = mg_batch_solve(b, f, x, tol, iters, relres, nullptr, stream);
+    std::string msg = g_err;
+    mg_batch_destroy(b);
+    g_err = msg;
+    return rc;
 }
 
 int mg_control(mg_handle h, const double* x, double* u, void* stream) {

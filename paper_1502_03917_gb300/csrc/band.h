@@ -48,6 +48,9 @@ template <typename T>
 size_t band_smem_bytes();
 template <typename T>
 cudaError_t band_prepare();
+// blocks of the step kernel that can be resident on one SM
+template <typename T>
+int band_blocks_per_sm();
 template <typename T>
 void launch_lsgs_band(const LevelP<T>& P, const T* f, const T* xin, T* xout, const BandGrid& g, cudaStream_t s);
 

@@ -403,6 +403,15 @@ cudaError_t band_prepare() {
 }
 
 template <typename T>
+int band_blocks_per_sm() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lsgs_band<T, band_threads<T>()>, 2 * band_threads<T>(),
+                                                      band_smem_bytes<T>()) != cudaSuccess)
+        return 1;
+    return b > 0 ? b : 1;
+}
+
+template <typename T>
 void launch_lsgs_band(const LevelP<T>& P, const T* f, const T* xin, T* xout, const BandGrid& g, cudaStream_t s) {
     constexpr int WT = band_threads<T>();
     launch_pdl(k_lsgs_band<T, WT>, dim3(g.nb, g.ns), 2 * WT, band_smem_bytes<T>(), s, P, f, xin, xout, g.W, g.Hs);
@@ -412,6 +421,8 @@ template size_t band_smem_bytes<float>();
 template size_t band_smem_bytes<double>();
 template cudaError_t band_prepare<float>();
 template cudaError_t band_prepare<double>();
+template int band_blocks_per_sm<float>();
+template int band_blocks_per_sm<double>();
 template void launch_lsgs_band<float>(const LevelP<float>&, const float*, const float*, float*, const BandGrid&,
                                       cudaStream_t);
 template void launch_lsgs_band<double>(const LevelP<double>&, const double*, const double*, double*,

@@ -15,6 +15,10 @@ namespace aaomg {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 #endif
 
+// Set while recording a graph that must not contain programmatic edges (the
+// launches then serialise fully; griddepcontrol.wait returns at once).
+inline thread_local bool g_pdl_off = false;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {
@@ -27,7 +31,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g_pdl_off ? 0 : 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 

@@ -392,7 +392,7 @@ cudaLaunchConfig_t strips_config(int cs, cudaStream_t s, cudaLaunchAttribute* at
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 0;
-    if (pdl) {
+    if (pdl && !g_pdl_off) {
         at[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl.h
         at[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
         ++cfg.numAttrs;

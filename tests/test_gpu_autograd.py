@@ -51,6 +51,34 @@ def test_autograd_matches_direct_solve_gradient(oracle_mod, alpha, precision):
     assert la.grad.item() == pytest.approx(alpha * g_alpha, rel=1e-8)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_batched_autograd_matches_direct_solve_gradient(oracle_mod, precision):
+    """Several desired states at one alpha through the batched Function (one
+    batch graph forward, one batched adjoint backward): each instance's dL/dyD
+    and the summed dL/dlog(alpha) equal the direct-solve gradients built from
+    the oracle's matrices."""
+    from paper_1502_03917_gb300.autograd import control
+
+    L, alpha, B = 5, 1e-2, 3
+    rng = np.random.default_rng(21)
+    yD_np = rng.uniform(-1.0, 1.0, (B, ((1 << L) + 1) ** 2))
+    ut_np = rng.standard_normal(yD_np.shape)
+    yD = dev(yD_np).requires_grad_(True)
+    la = torch.tensor(np.log(alpha), dtype=torch.float64, requires_grad=True)
+    u = control(yD, la, L, tol=1e-12, precision=precision)
+    assert u.shape == yD.shape
+    loss = 0.5 * ((u - dev(ut_np)) ** 2).sum()
+    loss.backward()
+    g_alpha = 0.0
+    for k in range(B):
+        g_yD, ga, u_ref = direct_gradient(oracle_mod, L, alpha, yD_np[k], ut_np[k])
+        np.testing.assert_allclose(u[k].detach().cpu().numpy(), u_ref, rtol=1e-8, atol=1e-8 * np.abs(u_ref).max())
+        gy = yD.grad[k].cpu().numpy()
+        assert np.linalg.norm(gy - g_yD) <= 1e-8 * np.linalg.norm(g_yD)
+        g_alpha += ga
+    assert la.grad.item() == pytest.approx(alpha * g_alpha, rel=1e-8)
+
+
 def test_autograd_finite_differences():
     import paper_1502_03917_gb300.aaomg as mg
 
@@ -109,3 +137,50 @@ def test_batch_solve_against_oracle(oracle_mod):
         assert torch.equal(x1, x)
     for s in solvers:
         s.close()
+
+
+def test_batch_graph_repeated_solves_and_statuses():
+    """A recorded batch (one CUDA graph, convergence tests on the device) can be
+    solved again with new initial guesses and tolerances; each instance gives
+    bitwise its own mg_solve's iterate, iteration count and residual history,
+    and an instance that runs out of iterations reports NOT_CONVERGED without
+    stopping the others."""
+    import paper_1502_03917_gb300.aaomg as mg
+
+    levels, alphas, yds = inputs.batch_instances(5, 9, lmin=4, lmax=7)
+    cfg = [("lsgs", "fp32_refine", 0), ("ne", "fp64", 0), ("cgs", "fp32_refine", 0), ("lsgs", "fp64", 2),
+           ("slsgs", "fp64", 0)]
+    solvers = [mg.Solver(L, a, smoother=sm, precision=p, max_iter=mi if mi else 200)
+               for (L, a, (sm, p, mi)) in zip(levels, alphas, cfg)]
+    fs = [s.rhs_from_yd(dev(y)) for s, y in zip(solvers, yds)]
+    with mg.Batch(solvers) as b:
+        for rep, tol in enumerate((1e-9, 1e-11)):
+            x0 = [dev(inputs.x_uniform(L, 50 + rep + k)) for k, L in enumerate(levels)]
+            xs = [x.clone() for x in x0]
+            its, rrs, sts, code = b.solve(fs, xs, tol=tol, raise_on_fail=False)
+            assert code == mg.ERR_NOT_CONVERGED
+            assert sts == [mg.OK, mg.OK, mg.OK, mg.ERR_NOT_CONVERGED, mg.OK]
+            assert its[3] == 2
+            hists = [s.history() for s in solvers]
+            for k, s in enumerate(solvers):
+                x1 = x0[k].clone()
+                it1, rr1, code1 = s.solve(fs[k], x1, tol=tol, raise_on_fail=False)
+                assert it1 == its[k] and rr1 == rrs[k]
+                assert torch.equal(x1, xs[k])
+                assert s.history() == hists[k]
+                if sts[k] == mg.OK:
+                    assert rrs[k] <= tol
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_bad_handles():
+    import paper_1502_03917_gb300.aaomg as mg
+
+    with mg.Solver(4, 1e-2) as a, mg.Solver(4, 1e-2, profile=True) as p:
+        with pytest.raises(mg.MGError) as e:
+            mg.Batch([a, a])
+        assert e.value.code == mg.ERR_BAD_ARG
+        with pytest.raises(mg.MGError) as e:
+            mg.Batch([a, p])
+        assert e.value.code == mg.ERR_BAD_ARG

@@ -177,6 +177,26 @@ def test_lsgs_step_kernel_tiling(mg, oracle_mod, L, tile, precision):
             assert d <= TOL[precision], (steps, d)
 
 
+@pytest.mark.parametrize("tile", [(0, 0), (0, 700), (100, 0)])
+@pytest.mark.parametrize("alpha", [1.0, 1e-8])
+def test_band_step_parity_L10(mg, oracle_mod, alpha, tile):
+    """The one-launch LSGS step at h = 2^-10 (1025^2 nodes, the size from which
+    the FP32 cycles use it), in the default tiling (bands of columns, one row
+    segment per block of a full wave), with tall segments and with narrow
+    bands, equals the oracle's multicolour sweep element by element."""
+    L = 10
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 1000))
+    f = inputs.f32_exact(inputs.x_uniform(L, 1001))
+    o = oracle_mod.Oracle(L, alpha, smoother="lsgs")
+    with mg.Solver(L, alpha, smoother="lsgs", precision="fp32_refine", tile_w=tile[0], tile_h=tile[1]) as s:
+        assert s.level_kernels()[L][0] == "band"
+        for steps in (1, 2):
+            x = dev(x0)
+            s.smooth(dev(f), x, steps)
+            d = field_diff(host(x), o.smooth(f, x0, steps), o.nn())
+            assert d <= TOL["fp32_refine"], (steps, d)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("L", [2, 4, 7])
 def test_transfer_parity(mg, oracle_mod, L, precision):
