@@ -41,19 +41,20 @@ UNIT = "unknowns/s"
 SWEEP_BYTES_FP32 = 24  # per node and sweep: read y, lambda, f_y, f_lambda; write y, lambda (4 B each)
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_L{L}.json")
 
-# DRAM bytes (read + written) of one finest-level LSGS step at h = 2^-11 from an
-# ncu capture of the band kernel, valid while the kernel's sources hash to SHA.
-BAND_TRAFFIC = {"level": 11, "bytes": 76_288_768,
-                "sha256": "a3c405f812c230ebbdf0f726695478e6274eb5cd90cb8df765dffaba08053bdc",
+# DRAM bytes (read + written) of one finest-level LSGS step (the band kernel)
+# from ncu captures (profiles/k_lsgs_band_l11.md, profiles/k_lsgs_band_l12.md),
+# per level; valid while the kernel's sources hash to SHA.
+BAND_TRAFFIC = {"bytes": {11: 76_288_768, 12: 387_372_032},
+                "sha256": "7aeef5c19847354be1d5f9f7174022fafa282b0a3e43cd952c9ea1f708fa7898",
                 "files": ["lsgs_band.cu", "band.h", "lean.cuh", "stencil.cuh", "common.cuh", "pair.cuh"]}
 
 
 def band_traffic(level):
-    """The captured traffic per launch, or None when the level differs or the
-    kernel has changed since the capture."""
+    """The captured traffic per launch, or None when the level was not
+    captured or the kernel has changed since the capture."""
     import hashlib
 
-    if level != BAND_TRAFFIC["level"]:
+    if level not in BAND_TRAFFIC["bytes"]:
         return None
     h = hashlib.sha256()
     try:
@@ -62,7 +63,7 @@ def band_traffic(level):
                 h.update(fh.read())
     except OSError:
         return None
-    return BAND_TRAFFIC["bytes"] if h.hexdigest() == BAND_TRAFFIC["sha256"] else None
+    return BAND_TRAFFIC["bytes"][level] if h.hexdigest() == BAND_TRAFFIC["sha256"] else None
 
 
 def parse():
@@ -557,9 +558,13 @@ def host_cpu():
 
 
 def run_e2e(args, solvers, yD, K, world, max_over_ranks, run_all):
-    """Same metric through mg_solve_host: f and x in pinned host memory, the
-    host-to-device and device-to-host copies inside the timed region."""
+    """Same metric through the public host-buffer API: f and x in pinned host
+    memory, the host-to-device and device-to-host copies inside the timed
+    region; the five solves as one batch (mg_batch_solve_host), or one after
+    another through mg_solve_host with --serial."""
     import torch
+
+    import paper_1502_03917_gb300.aaomg as mg
 
     N = next(iter(solvers.values())).N
     host_f = {}
@@ -569,6 +574,7 @@ def run_e2e(args, solvers, yD, K, world, max_over_ranks, run_all):
         hf.copy_(f)
         host_f[a] = hf
     hx = {a: torch.empty(2 * N, dtype=torch.float64, pin_memory=True) for a in solvers}
+    batch = None if args.serial else mg.Batch([solvers[a] for a in ALPHAS])
     torch.cuda.synchronize()
 
     def one(a):
@@ -576,7 +582,12 @@ def run_e2e(args, solvers, yD, K, world, max_over_ranks, run_all):
         solvers[a].solve_host(host_f[a].numpy(), hx[a].numpy(), tol=args.tol)
 
     def step():
-        run_all(one)
+        if batch is None:
+            run_all(one)
+            return
+        for a in ALPHAS:
+            hx[a].zero_()
+        batch.solve_host([host_f[a].numpy() for a in ALPHAS], [hx[a].numpy() for a in ALPHAS], tol=args.tol)
 
     step()  # warm-up
     torch.cuda.synchronize()
@@ -585,9 +596,12 @@ def run_e2e(args, solvers, yD, K, world, max_over_ranks, run_all):
         step()
     torch.cuda.synchronize()
     sec = max_over_ranks(time.perf_counter() - t0)
+    if batch is not None:
+        batch.close()
     n = len(solvers)
     return {"value": world * n * 2 * N * K / sec, "unit": UNIT, "h2d_bytes_per_step": n * 2 * (2 * N * 8),
-            "d2h_bytes_per_step": n * 2 * N * 8, "ms_per_step": 1e3 * sec / K}
+            "d2h_bytes_per_step": n * 2 * N * 8, "ms_per_step": 1e3 * sec / K,
+            "api": "mg_solve_host per alpha" if batch is None else "mg_batch_solve_host (five alphas, one graph)"}
 
 
 def oracle_iterations(L, smoother, tol):

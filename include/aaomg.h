@@ -204,6 +204,12 @@ AAOMG_API int mg_batch_create(int count, const mg_handle* handles, mg_batch* out
 AAOMG_API int mg_batch_solve(mg_batch b, const double* const* f, double* const* x, double tol, int* iters,
                              double* relres, int* status, void* stream);
 
+/* mg_batch_solve with f_host and x_host arrays of HOST pointers (pinned or
+ * pageable): the vectors are copied to the device, solved by one launch of the
+ * batch graph and copied back, all on `stream`. */
+AAOMG_API int mg_batch_solve_host(mg_batch b, const double* const* f_host, double* const* x_host, double tol,
+                                  int* iters, double* relres, int* status, void* stream);
+
 /* Batched adjoint of the solves (mg_adjoint for every instance at once): given
  * each instance's solution x_k of A_k x_k = (M y_D,k, 0) and ubar_k = dL/du_k
  * (N_k doubles), solves A_k z_k = (0, ubar_k / alpha_k) from zero to `tol` in

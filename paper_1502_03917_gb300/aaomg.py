@@ -97,6 +97,7 @@ def load():
             "mg_batch_create": (I, [I, ctypes.POINTER(H), ctypes.POINTER(H)]),
             "mg_batch_solve": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), D, pI, pD, pI, P]),
             "mg_batch_destroy": (None, [H]),
+            "mg_batch_solve_host": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), D, pI, pD, pI, P]),
             "mg_batch_adjoint": (I, [H, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                      pD, D, pI, P]),
             "mg_control": (I, [H, P, P, P]),
@@ -179,6 +180,27 @@ class Batch:
         code = self._lib.mg_batch_solve(self._b, fp, xp, float(tol), it, rr, st, _stream())
         if raise_on_fail:
             _check(code, "mg_batch_solve")
+        return list(it), list(rr), list(st), code
+
+    def solve_host(self, fs, xs, tol: float = 1e-8, raise_on_fail: bool = True):
+        """solve() with fs and xs contiguous float64 numpy arrays in host
+        memory (xs in/out): host-to-device and device-to-host copies inside."""
+        import numpy as np
+
+        n = len(self.solvers)
+        for s, f, x in zip(self.solvers, fs, xs):
+            for a in (f, x):
+                if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                        and a.size == 2 * s.N):
+                    raise TypeError("expected contiguous float64 numpy arrays of 2N elements")
+        fp = (ctypes.c_void_p * n)(*[f.ctypes.data for f in fs])
+        xp = (ctypes.c_void_p * n)(*[x.ctypes.data for x in xs])
+        it = (ctypes.c_int * n)()
+        rr = (ctypes.c_double * n)()
+        st = (ctypes.c_int * n)()
+        code = self._lib.mg_batch_solve_host(self._b, fp, xp, float(tol), it, rr, st, _stream())
+        if raise_on_fail:
+            _check(code, "mg_batch_solve_host")
         return list(it), list(rr), list(st), code
 
     def adjoint(self, xs, ubars, tol: float = 1e-10):

@@ -523,56 +523,91 @@ int build_class_table(mg_ctx* H, Lev& v, double km) {
 }
 
 // Autotuning: for every level, time the candidate smoothing kernels on the
-// level's own (zero) vectors -- a single block and every cluster size that can
-// run on levels up to small_max nodes per side; the band kernel against one
-// launch per colour phase for LSGS above -- and keep the fastest.  A call of 2
-// steps, once to warm up and then three times under CUDA events.
+// level's own vectors (zeroed at set-up) -- a single block and every cluster
+// size that can run on levels up to small_max nodes per side; for LSGS above,
+// one launch per colour phase against the band kernel in three tilings (the
+// default segments of one full wave, segments twice as tall, and half as tall:
+// two waves) -- and keep the fastest.  A candidate is a call of 2 steps, run
+// once to warm up and then five times under CUDA events; the median counts,
+// and a candidate replaces the level's default only if it is at least 5%
+// faster, so that timing noise does not flip the choice between set-ups.
 template <typename T>
 int autotune_levels(mg_ctx* H, double km) {
     TraceRange tr("autotune level kernels");
     cudaStream_t s = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
+    constexpr int kReps = 5;
+    cudaEvent_t ev[kReps + 1] = {};
     CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
+    for (auto& e : ev) CK(cudaEventCreate(&e));
     int rc = AAOMG_OK;
     auto timed = [&](auto&& call) -> float {
         call();
-        cudaEventRecord(a, s);
-        for (int r = 0; r < 3; ++r) call();
-        cudaEventRecord(b, s);
-        float ms = -1.f;
-        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess ||
-            cudaGetLastError() != cudaSuccess)
-            return -1.f;
-        return ms;
+        cudaEventRecord(ev[0], s);
+        for (int r = 0; r < kReps; ++r) {
+            call();
+            cudaEventRecord(ev[r + 1], s);
+        }
+        float ms[kReps];
+        if (cudaEventSynchronize(ev[kReps]) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -1.f;
+        for (int r = 0; r < kReps; ++r)
+            if (cudaEventElapsedTime(&ms[r], ev[r], ev[r + 1]) != cudaSuccess) return -1.f;
+        std::sort(ms, ms + kReps);
+        return ms[kReps / 2];
     };
+    constexpr float kMargin = 0.95f;  // a challenger must beat the default by 5%
     for (int l = 2; l <= H->L && !rc; ++l) {
         Lev& v = H->lev[l];
         if (v.n + 1 <= H->small_max && H->o.cluster_size == 0) {
             if (!v.ctab && (rc = build_class_table<T>(H, v, km))) break;
-            float best = -1.f;
-            int best_cs = v.cs;
+            const int dflt = v.cs;
+            float best = dflt > 0 ? timed([&] { smooth<T>(H, l, 2, s); }) : -1.f;
+            int best_cs = dflt;
             for (int cs : {1, 2, 4, 8, 16}) {
-                if (strips_max_active<T>(v.n, cs) <= 0) continue;
+                if (cs == dflt || strips_max_active<T>(v.n, cs) <= 0) continue;
                 v.cs = cs;
                 const float ms = timed([&] { smooth<T>(H, l, 2, s); });
-                if (ms >= 0.f && (best < 0.f || ms < best)) {
+                if (ms >= 0.f && (best < 0.f || ms < kMargin * best)) {
                     best = ms;
                     best_cs = cs;
                 }
             }
             v.cs = best_cs;
         } else if (v.cs == 0 && H->o.smoother == MG_SMOOTHER_LSGS && H->o.tile_w <= 0 && H->o.tile_h <= 0) {
-            v.band = true;
-            const float tb = timed([&] { smooth<T>(H, l, 2, s); });
-            v.band = false;
-            const float tp = timed([&] { smooth<T>(H, l, 2, s); });
-            v.band = tb >= 0.f && (tp < 0.f || tb < tp);
+            const bool dflt_band = v.band;
+            const BandGrid g0 = v.bg;
+            BandGrid cand[3] = {g0, g0, g0};
+            const int target = H->nsm * (H->fp32 ? band_blocks_per_sm<float>() : band_blocks_per_sm<double>());
+            auto with_segments = [&](int ns) {
+                ns = ns < 1 ? 1 : ns;
+                const int hs = (v.n + 1 + ns - 1) / ns;
+                return H->fp32 ? band_grid<float>(v.n, 0, hs, target) : band_grid<double>(v.n, 0, hs, target);
+            };
+            cand[1] = with_segments(g0.ns / 2);
+            cand[2] = with_segments(g0.ns * 2);
+            // the default first: phases or the default band tiling
+            v.band = dflt_band;
+            float best = timed([&] { smooth<T>(H, l, 2, s); });
+            bool best_band = dflt_band;
+            BandGrid best_g = g0;
+            auto challenge = [&](bool band, const BandGrid& g) {
+                if (band == dflt_band && (!band || (g.nb == g0.nb && g.ns == g0.ns))) return;
+                v.band = band;
+                v.bg = g;
+                const float ms = timed([&] { smooth<T>(H, l, 2, s); });
+                if (ms >= 0.f && (best < 0.f || ms < kMargin * best)) {
+                    best = ms;
+                    best_band = band;
+                    best_g = g;
+                }
+            };
+            challenge(false, g0);
+            for (const BandGrid& g : cand) challenge(true, g);
+            v.band = best_band;
+            v.bg = best_g;
         }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
     cudaStreamDestroy(s);
     if (!rc && cudaGetLastError() != cudaSuccess) rc = fail(AAOMG_ERR_CUDA, "autotuning launch failed");
     return rc;
@@ -1433,24 +1468,45 @@ int batch_finish(mg_batch b, cudaStream_t s, int* iters, double* relres, int* st
 
 extern "C" {
 
-int mg_batch_solve(mg_batch b, const double* const* f, double* const* x, double tol, int* iters, double* relres,
-                   int* status, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// mg_batch_solve with the vectors in device memory (D2D copies) or in host
+// memory (H2D in, D2H out); the copies are ordered on s around the launch.
+int batch_solve_copy(mg_batch b, const double* const* f, double* const* x, double tol, int* iters, double* relres,
+                     int* status, cudaStream_t s, bool host) {
     if (!b || !f || !x || !(tol >= 0.0)) return fail(AAOMG_ERR_BAD_ARG, "bad batch arguments");
     for (int k = 0; k < b->count; ++k)
         if (!f[k] || !x[k]) return fail(AAOMG_ERR_BAD_ARG, "null vector in batch");
     int rc = check_handle(b->H[0]);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     for (int k = 0; k < b->count; ++k) {
         mg_ctx* H = b->H[k];
         size_t bytes = (size_t)vec_bytes(H);
-        CK(cudaMemcpyAsync(iter_f(H), f[k], bytes, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(iter_x(H), x[k], bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(iter_f(H), f[k], bytes, in, s));
+        CK(cudaMemcpyAsync(iter_x(H), x[k], bytes, in, s));
     }
     if ((rc = batch_launch(b, tol, s))) return rc;
     for (int k = 0; k < b->count; ++k)
-        CK(cudaMemcpyAsync(x[k], iter_x(b->H[k]), (size_t)vec_bytes(b->H[k]), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(x[k], iter_x(b->H[k]), (size_t)vec_bytes(b->H[k]), out, s));
     return batch_finish(b, s, iters, relres, status);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_batch_solve(mg_batch b, const double* const* f, double* const* x, double tol, int* iters, double* relres,
+                   int* status, void* stream) {
+    return batch_solve_copy(b, f, x, tol, iters, relres, status, (cudaStream_t)stream, false);
+}
+
+int mg_batch_solve_host(mg_batch b, const double* const* f_host, double* const* x_host, double tol, int* iters,
+                        double* relres, int* status, void* stream) {
+    return batch_solve_copy(b, f_host, x_host, tol, iters, relres, status, (cudaStream_t)stream, true);
 }
 
 int mg_batch_adjoint(mg_batch b, const double* const* x, const double* const* ubar, double* const* z,

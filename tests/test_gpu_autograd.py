@@ -184,3 +184,24 @@ def test_batch_rejects_bad_handles():
         with pytest.raises(mg.MGError) as e:
             mg.Batch([a, p])
         assert e.value.code == mg.ERR_BAD_ARG
+
+
+def test_batch_solve_host_equals_device():
+    """mg_batch_solve_host (host vectors, copies inside the call) gives bitwise
+    the iterates, counts and residuals of mg_batch_solve on device vectors."""
+    import paper_1502_03917_gb300.aaomg as mg
+
+    levels, alphas, yds = inputs.batch_instances(3, 11, lmin=4, lmax=7)
+    solvers = [mg.Solver(L, a, smoother="lsgs", precision="fp32_refine") for L, a in zip(levels, alphas)]
+    fs = [s.rhs_from_yd(dev(y)) for s, y in zip(solvers, yds)]
+    with mg.Batch(solvers) as b:
+        xs = [torch.zeros_like(f) for f in fs]
+        its, rrs, sts, code = b.solve(fs, xs, tol=1e-10)
+        hf = [f.cpu().numpy().copy() for f in fs]
+        hx = [np.zeros(f.numel()) for f in fs]
+        its_h, rrs_h, sts_h, code_h = b.solve_host(hf, hx, tol=1e-10)
+    assert code == code_h == mg.OK and its == its_h and rrs == rrs_h and sts == sts_h
+    for x, xh in zip(xs, hx):
+        assert np.array_equal(x.cpu().numpy(), xh)
+    for s in solvers:
+        s.close()

@@ -120,13 +120,15 @@ def test_cluster_smoothing_call(mg, oracle_mod, L, cs, smoother, precision):
             assert d <= TOL[precision], (steps, d)
 
 
+@pytest.mark.parametrize("L", [9, 10])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("smoother", ["lsgs", "cgs"])
-def test_autotuned_kernels(mg, oracle_mod, smoother, precision):
-    """With autotune the set-up picks each level's kernel by timing; whatever
-    it picks, a smoothing call still gives the oracle's steps and a solve the
-    oracle's solution."""
-    L, alpha = 9, 1e-2
+def test_autotuned_kernels(mg, oracle_mod, smoother, precision, L):
+    """With autotune the set-up picks each level's kernel by timing (strips
+    cluster sizes; per-phase launches or the band kernel in one of three
+    tilings); whatever it picks, a smoothing call still gives the oracle's
+    steps and a solve the oracle's solution."""
+    alpha = 1e-2
     x0 = inputs.f32_exact(inputs.x_uniform(L, 900))
     f = inputs.f32_exact(inputs.x_uniform(L, 901))
     o = oracle_mod.Oracle(L, alpha, smoother=smoother)
