@@ -44,8 +44,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_L{L}.json")
 # DRAM bytes (read + written) of one finest-level LSGS step (the band kernel)
 # from ncu captures (profiles/k_lsgs_band_l11.md, profiles/k_lsgs_band_l12.md),
 # per level; valid while the kernel's sources hash to SHA.
-BAND_TRAFFIC = {"bytes": {11: 76_288_768, 12: 387_372_032},
-                "sha256": "7aeef5c19847354be1d5f9f7174022fafa282b0a3e43cd952c9ea1f708fa7898",
+BAND_TRAFFIC = {"bytes": {11: 74_252_032, 12: 388_913_664},
+                "sha256": "a3995fed71852695333d4747006488eae912eb8f6379288f7370fb8e61d052d2",
                 "files": ["lsgs_band.cu", "band.h", "lean.cuh", "stencil.cuh", "common.cuh", "pair.cuh"]}
 
 
@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-vcycle", action="store_true", help="skip the V-cycle comparison")
     p.add_argument("--inner-cycles", type=int, default=0, help="FP32 cycles per refinement step (0: library default)")
+    p.add_argument("--small-max", type=int, default=0,
+                   help="largest level (nodes per side) smoothed in one launch per call (0: library default 513; "
+                        "257: per-phase launches on 513^2)")
     p.add_argument("--autotune", action="store_true",
                    help="let the library time each level's candidate kernels at set-up")
     p.add_argument("--batch", type=int, default=0,
@@ -209,7 +212,8 @@ def run_ours(args, rank, world, local):
 
     def make(precision, profile):
         return {a: mg.Solver(L, a, smoother=args.smoother, precision=precision, cycle=args.cycle, max_iter=100,
-                             profile=profile, inner_cycles=args.inner_cycles, autotune=args.autotune)
+                             profile=profile, inner_cycles=args.inner_cycles, autotune=args.autotune,
+                             small_max=args.small_max)
                 for a in ALPHAS}
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2

@@ -95,7 +95,10 @@ typedef struct mg_options {
     int tile_w;       /* LSGS step kernel: owned columns per block; <= 0: widest the block allows */
     int tile_h;       /* LSGS step kernel: owned rows per block; <= 0: chosen to fill the GPU */
     int small_max;    /* levels with at most this many nodes per side smooth in one launch per
-                         smoothing call (one block or one cluster); 0: 257; < 0: never */
+                         smoothing call (one block or one cluster: x and the residual in shared
+                         memory up to 257 nodes per side; at 513, FP32 LSGS and sLSGS only, a
+                         16-block cluster with the residual in shared memory and x in global
+                         memory); 0: 513; < 0: never */
     int cluster_size; /* blocks per cluster of that launch on levels with 65, 129 or 257 nodes per
                          side (2..16); 0: by level size and precision (FP32: one block, 16, 16;
                          FP64: 8, 16, 16); 1: one block where it fits, else a launch per colour

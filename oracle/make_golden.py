@@ -15,7 +15,9 @@ stalls the residual a little below that); the file keeps the residual history
 (so the iteration count to any tolerance above 1e-10 can be read off), and the
 solution at 256 seeded node indices.
 
-Usage: python oracle/make_golden.py [L]   (tens of minutes per solve on one core)
+Usage: python oracle/make_golden.py [L [smoother ...]]   (minutes per solve on one core)
+With smoothers named, only their runs are computed and merged into an existing
+file (sLSGS with 1+1 smoothing steps, the paper's choice; the others 2+2).
 """
 import json
 import os
@@ -47,11 +49,17 @@ def main():
     yD = w["yd"](L)
     nn = ((1 << L) + 1) ** 2
     sample = np.sort(np.random.default_rng(12345).choice(nn, size=256, replace=False))
+    smoothers = tuple(sys.argv[2:]) or w["smoothers"]
     res = {"level": L, "workload": w["workload"], "sample_nodes": sample.tolist(), "runs": []}
-    for smoother in w["smoothers"]:
+    if sys.argv[2:] and os.path.exists(out):
+        res = json.load(open(out))
+        assert res["sample_nodes"] == sample.tolist()
+        res["runs"] = [r for r in res["runs"] if r["smoother"] not in smoothers]
+    for smoother in smoothers:
+        nu = 1 if smoother == "slsgs" else 2
         for a in w["alphas"]:
             t0 = time.time()
-            o = oracle.Oracle(L, a, smoother=smoother)
+            o = oracle.Oracle(L, a, smoother=smoother, nu_pre=nu, nu_post=nu)
             f = o.rhs(yD)
             x, it, rr, hist = o.solve(f, tol=1e-10, max_iter=60)
             res["runs"].append({

@@ -48,6 +48,7 @@ struct Lev {
     BandGrid bg{};
     int cs = 0;              // smoothing calls in one launch: of one block (1) or a cluster of cs blocks; 0: no
     bool band = false;       // LSGS steps by the one-launch band kernel (else one launch per colour phase)
+    bool rg = false;         // whole smoothing calls by the 513^2 cluster kernel (residual on chip, x in global)
     void* ctab = nullptr;    // its boundary-class table (EdgeClass[25] in the cycles' precision)
     LevelP<float> pf{};
     LevelP<double> pd{};
@@ -208,7 +209,7 @@ struct mg_ctx {
     int dev = 0;
     int nsm = 152;
     int band_min = 1025;      // FP32 levels with at least this many nodes per side use the one-launch LSGS step
-    int small_max = 257;      // levels up to this many nodes per side: one launch per smoothing call
+    int small_max = 513;      // levels up to this many nodes per side: one launch per smoothing call
     bool fp32 = false;
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
@@ -365,6 +366,13 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
     T* x = (T*)v.x;
     T* f = (T*)v.f;
     T* rh = (T*)v.rh;
+    if (v.rg) {
+        // the whole LSGS / sLSGS smoothing call in one launch of a 16-block
+        // cluster (rh in shared memory, x updated in global memory)
+        launch_smooth_rg<T>(P, (const EdgeClass<T>*)v.ctab, H->o.smoother, steps, x, f, s);
+        H->rec_kernels += 1;
+        return;
+    }
     if (v.cs > 0) {
         // the whole smoothing call in one launch of one block or one cluster
         // (x and rh, or for CGS x and f, in shared memory)
@@ -557,7 +565,7 @@ int autotune_levels(mg_ctx* H, double km) {
     constexpr float kMargin = 0.95f;  // a challenger must beat the default by 5%
     for (int l = 2; l <= H->L && !rc; ++l) {
         Lev& v = H->lev[l];
-        if (v.n + 1 <= H->small_max && H->o.cluster_size == 0) {
+        if (v.n + 1 <= H->small_max && H->o.cluster_size == 0 && !v.rg) {
             if (!v.ctab && (rc = build_class_table<T>(H, v, km))) break;
             const int dflt = v.cs;
             float best = dflt > 0 ? timed([&] { smooth<T>(H, l, 2, s); }) : -1.f;
@@ -572,38 +580,45 @@ int autotune_levels(mg_ctx* H, double km) {
                 }
             }
             v.cs = best_cs;
-        } else if (v.cs == 0 && H->o.smoother == MG_SMOOTHER_LSGS && H->o.tile_w <= 0 && H->o.tile_h <= 0) {
-            const bool dflt_band = v.band;
+        } else if (v.cs == 0 && H->o.tile_w <= 0 && H->o.tile_h <= 0 &&
+                   (H->o.smoother == MG_SMOOTHER_LSGS || (H->o.smoother == MG_SMOOTHER_SLSGS && v.rg))) {
+            // candidates: one launch per colour phase (kind 0), the band
+            // kernel in three tilings (kind 1, LSGS), the 513^2 cluster
+            // kernel (kind 2, where it runs)
+            const bool lsgs = H->o.smoother == MG_SMOOTHER_LSGS;
+            const int dflt_kind = v.rg ? 2 : (v.band ? 1 : 0);
             const BandGrid g0 = v.bg;
-            BandGrid cand[3] = {g0, g0, g0};
             const int target = H->nsm * (H->fp32 ? band_blocks_per_sm<float>() : band_blocks_per_sm<double>());
             auto with_segments = [&](int ns) {
                 ns = ns < 1 ? 1 : ns;
                 const int hs = (v.n + 1 + ns - 1) / ns;
                 return H->fp32 ? band_grid<float>(v.n, 0, hs, target) : band_grid<double>(v.n, 0, hs, target);
             };
-            cand[1] = with_segments(g0.ns / 2);
-            cand[2] = with_segments(g0.ns * 2);
-            // the default first: phases or the default band tiling
-            v.band = dflt_band;
-            float best = timed([&] { smooth<T>(H, l, 2, s); });
-            bool best_band = dflt_band;
-            BandGrid best_g = g0;
-            auto challenge = [&](bool band, const BandGrid& g) {
-                if (band == dflt_band && (!band || (g.nb == g0.nb && g.ns == g0.ns))) return;
-                v.band = band;
+            const BandGrid cand[3] = {g0, with_segments(g0.ns / 2), with_segments(g0.ns * 2)};
+            auto set = [&](int kind, const BandGrid& g) {
+                v.rg = kind == 2;
+                v.band = kind == 1;
                 v.bg = g;
+            };
+            set(dflt_kind, g0);
+            float best = timed([&] { smooth<T>(H, l, 2, s); });
+            int best_kind = dflt_kind;
+            BandGrid best_g = g0;
+            auto challenge = [&](int kind, const BandGrid& g) {
+                if (kind == dflt_kind && (kind != 1 || (g.nb == g0.nb && g.ns == g0.ns))) return;
+                set(kind, g);
                 const float ms = timed([&] { smooth<T>(H, l, 2, s); });
                 if (ms >= 0.f && (best < 0.f || ms < kMargin * best)) {
                     best = ms;
-                    best_band = band;
+                    best_kind = kind;
                     best_g = g;
                 }
             };
-            challenge(false, g0);
-            for (const BandGrid& g : cand) challenge(true, g);
-            v.band = best_band;
-            v.bg = best_g;
+            challenge(0, g0);
+            if (lsgs)
+                for (const BandGrid& g : cand) challenge(1, g);
+            if (dflt_kind == 2) challenge(2, g0);
+            set(best_kind, best_g);
         }
     }
     for (auto& e : ev)
@@ -1048,6 +1063,13 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         }
         if (!rc && v.cs > 0)
             rc = H->fp32 ? build_class_table<float>(H, v, km) : build_class_table<double>(H, v, km);
+        // 513 x 513 nodes (FP32 LSGS or sLSGS): the cluster kernel that keeps
+        // only the residual on chip
+        if (!rc && v.cs == 0 && H->fp32 && o.cluster_size == 0 &&
+            (o.smoother == MG_SMOOTHER_LSGS || o.smoother == MG_SMOOTHER_SLSGS) && rg_max_active<float>(v.n) > 0) {
+            v.rg = true;
+            rc = build_class_table<float>(H, v, km);
+        }
     }
     if (!rc && o.autotune) rc = H->fp32 ? autotune_levels<float>(H, km) : autotune_levels<double>(H, km);
     if (rc) {
@@ -1156,6 +1178,9 @@ int mg_level_kernel(mg_handle h, int level, int* kind, int* blocks) {
     int k = MG_KERNEL_PHASES, b = 0;
     if (level == 1 || level <= h->lc || (h->ld > 0 && level <= h->ld)) {
         k = MG_KERNEL_COARSE;
+    } else if (v.rg) {
+        k = MG_KERNEL_STRIPS;
+        b = 16;
     } else if (v.cs > 0) {
         k = MG_KERNEL_STRIPS;
         b = v.cs;

@@ -383,6 +383,198 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
     }
 }
 
+// ------------------------------------ level 513^2: residual on chip only --
+// On the level with 513 x 513 nodes the iterate and the residual of a 16-block
+// cluster's strips (4.2 MB in FP32) do not fit in shared memory, the residual
+// alone does (33 rows of (y, lambda) pairs, 135 KB per block).  This kernel
+// keeps the scaled residual on chip for the whole smoothing call and updates
+// the iterate in place in global memory (L2-resident): in an LSGS phase each
+// update writes one field of one node, which only the updating thread touches,
+// and the residual at the start of the call is the only place that reads a
+// node's neighbours' x.  LSGS and sLSGS only (NE recomputes the residual from
+// x every step, CGS reads its neighbours' x in every phase).
+template <typename T>
+struct RhLocal {  // the strip's residual pairs addressed by global node index
+    typename P2<T>::t* r;
+    int64_t off;
+    __device__ __forceinline__ T& y(int64_t p) const { return r[p - off].x; }
+    __device__ __forceinline__ T& l(int64_t p) const { return r[p - off].y; }
+};
+
+// Algorithm 2 update of (field, node (i, j)) on the residual rows: gather,
+// p = q / N_ii, scatter; returns p (the caller adds it to x)
+template <typename T, typename V2>
+__device__ __forceinline__ T rg_lsgs_fast(const LevelP<T>& P, int field, V2* rs, V2* rsp, V2* rsm, int i) {
+    V2 M, K, nb[7];
+    rows_stencil(rs, rsp, rsm, i, psplat(P.mC), psplat(P.mO), M, K, nb);
+    T qy, ql;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T pv = field == 0 ? qy * P.invNy_int : ql * P.invNl_int;
+    const V2 mp = psplat(-pv);
+    const V2 cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
+    const V2 cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
+    const V2 cD = pmake<T>(P.sc[field][2][0], P.sc[field][2][1]);
+    rs[i] = pfma(mp, cC, nb[0]);
+    rs[i + 1] = pfma(mp, cE, nb[1]);
+    rs[i - 1] = pfma(mp, cE, nb[2]);
+    rsp[i] = pfma(mp, cE, nb[3]);
+    rsm[i] = pfma(mp, cE, nb[4]);
+    rsp[i + 1] = pfma(mp, cD, nb[5]);
+    rsm[i - 1] = pfma(mp, cD, nb[6]);
+    return pv;
+}
+
+template <typename T, int N, class S_>
+__device__ __forceinline__ T rg_lsgs_edge(const LevelP<T>& P, const EdgeClass<T>& C, int field, const S_& S, int i,
+                                          int j) {
+    using V2 = typename P2<T>::t;
+    V2 sc[7];  // read before the first store
+#pragma unroll
+    for (int o = 0; o < 7; ++o) sc[o] = pmake<T>(C.sc[field][o][0], C.sc[field][o][1]);
+    const T inv_nd = field == 0 ? C.iny : C.inl;
+    V2* const rows[3] = {S.rrow(j - 1), S.rrow(j), S.rrow(j + 1)};
+    V2 v[7];
+    T My, Ky, Ml, Kl, qy, ql;
+    cl_gather<T, N>(rows, i, j, C, v, My, Ky, Ml, Kl);
+    rows_from_dots(P, My, Ky, Ml, Kl, qy, ql);
+    const T p = (field == 0 ? qy : ql) * inv_nd;
+    const V2 mp = psplat(-p);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        const int ii = i + DI(o), jj = j + DJ(o);
+        if (in_grid(ii, jj, N)) rows[DJ(o) + 1][ii] = pfma(mp, sc[o], v[o]);
+    }
+    return p;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(strip_threads<T>()) k_smooth_rg(LevelP<T> P, const EdgeClass<T>* __restrict__ ctab,
+                                                                  int smoother, int steps, T* __restrict__ x,
+                                                                  const T* __restrict__ f) {
+    pdl_wait();
+    using V2 = typename P2<T>::t;
+    constexpr int LD = N + 1;
+    constexpr int W = N - 3;              // deep-interior columns
+    constexpr int CPR = (N - 3 + 6) / 7;  // slots per row of one colour
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* R = reinterpret_cast<V2*>(smem_raw);
+    __shared__ EdgeClass<T> s_cls[25];
+
+    Strip<T, N, true> S;
+    S.r0 = strip_row_lo(rank, N + 1, cs);
+    S.r1 = strip_row_lo(rank + 1, N + 1, cs);
+    S.X = S.Xb = S.Xa = nullptr;  // the iterate stays in global memory
+    S.R = R;
+    S.Rb = S.Ra = nullptr;
+    if (rank > 0) {
+        const int lb = S.r0 - 1 - strip_row_lo(rank - 1, N + 1, cs);  // local index of row r0-1 below
+        S.Rb = cl.map_shared_rank(R, rank - 1) + lb * LD;
+    }
+    if (rank < cs - 1) S.Ra = cl.map_shared_rank(R, rank + 1);
+
+    const int g = threadIdx.x, G = blockDim.x;
+    {
+        constexpr int words = 25 * sizeof(EdgeClass<T>) / sizeof(T);
+        T* dst = reinterpret_cast<T*>(s_cls);
+        const T* src = reinterpret_cast<const T*>(ctab);
+        for (int t = g; t < words; t += G) dst[t] = src[t];
+    }
+    // the residual L^{-1}(f - A x) of the strip's nodes from global x and f:
+    // the constant interior stencil where the whole neighbourhood is interior,
+    // the general stencil on the two rows and columns along the boundary
+    const RhLocal<T> rl{R, (int64_t)S.r0 * LD};
+    for (int t = g; t < (S.r1 - S.r0) * LD; t += G) {
+        const int j = S.r0 + t / LD, i = t - (j - S.r0) * LD;
+        if (i >= 2 && i <= N - 2 && j >= 2 && j <= N - 2) {
+            const int64_t p = (int64_t)j * LD + i;
+            const T* xl = x + P.fs;
+            const T y4 = (x[p + 1] + x[p - 1]) + (x[p + LD] + x[p - LD]);
+            const T l4 = (xl[p + 1] + xl[p - 1]) + (xl[p + LD] + xl[p - LD]);
+            const T y6 = y4 + (x[p + LD + 1] + x[p - LD - 1]);
+            const T l6 = l4 + (xl[p + LD + 1] + xl[p - LD - 1]);
+            const T My = P.mC * x[p] + P.mO * y6, Ml = P.mC * xl[p] + P.mO * l6;
+            const T Ky = T(4) * x[p] - y4, Kl = T(4) * xl[p] - l4;
+            T ay, al;
+            rows_from_dots(P, My, Ky, Ml, Kl, ay, al);
+            const T il = P.invLy_int;
+            R[t] = pmake<T>((f[p] - ay) * il, (f[p + P.fs] - al) * (il * P.invd));
+        } else {
+            resid_hat_acc(P, f, x, rl, i, j);
+        }
+    }
+    // every block has its residual and is running before any remote access
+    cluster_barrier();
+
+    const int ja = max(S.r0, 2), jb = min(S.r1, N - 1);
+    const int nrows = jb > ja ? jb - ja : 0;
+    StripEdges<N> SE;
+    SE.first_full_hi = rank == 0 ? 2 : 0;
+    SE.nfull = SE.first_full_hi + (rank == cs - 1 ? 2 : 0);
+    SE.ja = ja;
+    SE.nrows = nrows;
+    (void)W;
+
+    // A thread's slots of a phase are handled kSlots at a time: first every
+    // slot's node and its x value (one round of L2 loads in flight together),
+    // then the updates.
+    constexpr int kSlots = 3;
+    auto phase = [&](int field, int c) {
+        const int ni = nrows * CPR, nip = (ni + 31) & ~31;
+        const int ne = SE.count(c);
+        const int64_t foff = field ? P.fs : 0;
+        for (int t0 = g; t0 < nip + ne; t0 += kSlots * G) {
+            int si[kSlots], sj[kSlots], kind[kSlots];  // kind 0: none, 1: interior, 2: edge
+            T xv[kSlots];
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) {
+                const int t = t0 + q * G;
+                kind[q] = 0;
+                si[q] = sj[q] = 0;
+                if (t < nip) {
+                    if (t < ni) {
+                        const int r = t / CPR, k = t - r * CPR, j = ja + r;
+                        const int i = 2 + ((c - 2 * j - 2) % 7 + 7) % 7 + 7 * k;
+                        if (i <= N - 2) {
+                            kind[q] = 1;
+                            si[q] = i;
+                            sj[q] = j;
+                        }
+                    }
+                } else if (t < nip + ne) {
+                    int i, j;
+                    if (SE.node(t - nip, c, i, j)) {
+                        kind[q] = 2;
+                        si[q] = i;
+                        sj[q] = j;
+                    }
+                }
+                xv[q] = kind[q] ? x[(int64_t)sj[q] * LD + si[q] + foff] : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) {
+                if (!kind[q]) continue;
+                const int i = si[q], j = sj[q];
+                const T pv = kind[q] == 1
+                                 ? rg_lsgs_fast<T>(P, field, S.rrow(j), S.rrow(j + 1), S.rrow(j - 1), i)
+                                 : rg_lsgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], field, S, i, j);
+                x[(int64_t)j * LD + i + foff] = xv[q] + pv;
+            }
+        }
+        cluster_barrier();
+    };
+    for (int m = 0; m < steps; ++m) {
+        for (int field = 0; field < 2; ++field)
+            for (int c = 0; c < 7; ++c) phase(field, colour_seq(c));
+        if (smoother == 2)
+            for (int field = 1; field >= 0; --field)
+                for (int c = 6; c >= 0; --c) phase(field, colour_seq(c));
+    }
+}
+
 template <typename T, int N, bool CL>
 cudaLaunchConfig_t strips_config(int cs, cudaStream_t s, cudaLaunchAttribute* at, bool pdl = true) {
     cudaLaunchConfig_t cfg = {};
@@ -499,13 +691,78 @@ cudaError_t launch_smooth_strips(const LevelP<T>& P, const EdgeClass<T>* ctab, i
     }
 }
 
+// ---------------------------------------------- the 513^2 cluster kernel --
+constexpr int kRgN = 512;    // cells per side of the level it serves
+constexpr int kRgBlocks = 16;
+
+template <typename T>
+size_t rg_smem() {
+    const size_t rmax = (size_t)(kRgN + 1 + kRgBlocks - 1) / kRgBlocks;
+    return rmax * (kRgN + 1) * sizeof(typename P2<T>::t);
+}
+
+namespace {
+template <typename T>
+cudaLaunchConfig_t rg_config(cudaStream_t s, cudaLaunchAttribute* at, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kRgBlocks, 1, 1);
+    cfg.blockDim = dim3(strip_threads<T>(), 1, 1);
+    cfg.dynamicSmemBytes = rg_smem<T>();
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 0;
+    if (pdl && !g_pdl_off) {
+        at[cfg.numAttrs].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl.h
+        at[cfg.numAttrs].val.programmaticStreamSerializationAllowed = 1;
+        ++cfg.numAttrs;
+    }
+    at[cfg.numAttrs].id = cudaLaunchAttributeClusterDimension;
+    at[cfg.numAttrs].val.clusterDim.x = kRgBlocks;
+    at[cfg.numAttrs].val.clusterDim.y = 1;
+    at[cfg.numAttrs].val.clusterDim.z = 1;
+    ++cfg.numAttrs;
+    return cfg;
+}
+}  // namespace
+
+template <typename T>
+int rg_max_active(int n) {
+    if (sizeof(T) != 4 || n != kRgN || rg_smem<T>() > (size_t)kStripSmemMax) return 0;
+    if (cudaFuncSetAttribute(k_smooth_rg<T, kRgN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStripSmemMax) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_smooth_rg<T, kRgN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = rg_config<T>(0, at, false);
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, (void*)k_smooth_rg<T, kRgN>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return num;
+}
+
+template <typename T>
+cudaError_t launch_smooth_rg(const LevelP<T>& P, const EdgeClass<T>* ctab, int smoother, int steps, T* x, const T* f,
+                             cudaStream_t s) {
+    if (sizeof(T) != 4 || P.n != kRgN || (smoother != 1 && smoother != 2)) return cudaErrorInvalidValue;
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = rg_config<T>(s, at, true);
+    return cudaLaunchKernelEx(&cfg, k_smooth_rg<T, kRgN>, P, ctab, smoother, steps, x, f);
+}
+
 #define AAOMG_STRIPS_INST(T)                                                                                    \
     template size_t strips_smem<T>(int, int);                                                                   \
     template cudaError_t strips_prepare<T>();                                                                   \
     template bool strips_fit<T>(int, int);                                                                      \
     template int strips_max_active<T>(int, int);                                                                \
     template cudaError_t launch_smooth_strips<T>(const LevelP<T>&, const EdgeClass<T>*, int, int, T*, const T*, int, \
-                                                 cudaStream_t);
+                                                 cudaStream_t);                                                 \
+    template int rg_max_active<T>(int);                                                                         \
+    template cudaError_t launch_smooth_rg<T>(const LevelP<T>&, const EdgeClass<T>*, int, int, T*, const T*,     \
+                                             cudaStream_t);
 AAOMG_STRIPS_INST(float)
 AAOMG_STRIPS_INST(double)
 

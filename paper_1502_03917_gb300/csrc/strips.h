@@ -55,4 +55,14 @@ template <typename T>
 cudaError_t launch_smooth_strips(const LevelP<T>& P, const EdgeClass<T>* ctab, int smoother, int steps, T* x,
                                  const T* f, int cs, cudaStream_t s);
 
+// The level with 512 cells per side (FP32, LSGS or sLSGS): a whole smoothing
+// call in one launch of a 16-block cluster that keeps the residual in shared
+// memory and updates the iterate in global memory.  Clusters that can be
+// resident at once (0: cannot run: FP64, another size, no room).
+template <typename T>
+int rg_max_active(int n);
+template <typename T>
+cudaError_t launch_smooth_rg(const LevelP<T>& P, const EdgeClass<T>* ctab, int smoother, int steps, T* x,
+                             const T* f, cudaStream_t s);
+
 }  // namespace aaomg

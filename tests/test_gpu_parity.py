@@ -364,14 +364,50 @@ def test_protocol_iterations_match_oracle(mg, oracle_mod, k, alpha, smoother):
 def test_default_level_kernels(mg):
     """The per-level kernels of the default FP32 LSGS configuration at
     h = 2^-11: the dense level-5 map below, one block on level 6, clusters of
-    16 blocks on levels 7 and 8, per-phase launches on level 9, the band kernel
-    on levels 10 and 11 (the choices the set-up autotuner makes on GB300)."""
+    16 blocks on levels 7 and 8 (x and residual on chip) and on level 9 (the
+    residual on chip, x in global memory), the band kernel on levels 10 and
+    11; FP64 keeps one launch per colour phase on level 9."""
     with mg.Solver(11, 1e-2, smoother="lsgs", precision="fp32_refine") as s:
         k = s.level_kernels()
     assert [k[l][0] for l in range(1, 6)] == ["coarse"] * 5
     assert k[6] == ("strips", 1) and k[7] == ("strips", 16) and k[8] == ("strips", 16)
-    assert k[9] == ("phases", 0)
+    assert k[9] == ("strips", 16)
     assert all(k[l][0] == "band" and k[l][1] > 0 for l in (10, 11))
+    with mg.Solver(10, 1e-2, smoother="lsgs", precision="fp64") as s:
+        assert s.level_kernels()[9] == ("phases", 0)
+    with mg.Solver(10, 1e-2, smoother="cgs", precision="fp32_refine") as s:
+        assert s.level_kernels()[9] == ("phases", 0)
+
+
+@pytest.mark.parametrize("smoother", ["lsgs", "slsgs"])
+@pytest.mark.parametrize("alpha", [1.0, 1e-8])
+def test_level_513_cluster_kernel(mg, oracle_mod, smoother, alpha):
+    """The 513 x 513 cluster kernel (residual in the 16 blocks' shared memory,
+    iterate updated in global memory) gives the oracle's smoothing steps, one
+    step and a call of three, and a W-cycle of a h = 2^-10 problem that visits
+    it matches one with per-phase launches there (small_max = 257)."""
+    L = 9
+    x0 = inputs.f32_exact(inputs.x_uniform(L, 1100))
+    f = inputs.f32_exact(inputs.x_uniform(L, 1101))
+    o = oracle_mod.Oracle(L, alpha, smoother=smoother)
+    with mg.Solver(L, alpha, smoother=smoother, precision="fp32_refine") as s:
+        assert s.level_kernels()[L] == ("strips", 16)
+        for steps in (1, 3):
+            x = dev(x0)
+            s.smooth(dev(f), x, steps)
+            d = field_diff(host(x), o.smooth(f, x0, steps), o.nn())
+            assert d <= TOL["fp32_refine"], (steps, d)
+    yD = dev(inputs.yd_uniform(10, 3))
+    out = []
+    for small_max in (0, 257):
+        with mg.Solver(10, alpha, smoother=smoother, precision="fp32_refine", small_max=small_max) as s:
+            assert s.level_kernels()[9] == (("strips", 16) if small_max == 0 else ("phases", 0))
+            fs = s.rhs_from_yd(yD)
+            x = torch.zeros_like(fs)
+            s.solve(fs, x, tol=1e-10)
+            out.append(host(x))
+    n = out[0].size // 2
+    assert field_diff(out[0], out[1], n) <= 1e-8
 
 
 def test_profile_of_one_level(mg):
