@@ -5,7 +5,8 @@ Workloads (W-cycle with 2+2 smoothing steps down to h = 1/2):
 
 * L = 11 (default), the scaling workload at its largest size: h = 2^-11
   (2049 x 2049 nodes, 8.4M unknowns), y_D = sin(2 pi x) sin(2 pi y) +
-  0.1 N(0,1) (seed 1), alpha in {1, 1e-2, 1e-4, 1e-6, 1e-8}, NE and LSGS.
+  0.1 N(0,1) (seed 1), alpha in {1, 1e-2, 1e-4, 1e-6, 1e-8}, LSGS, NE, sLSGS
+  and CGS.
 * L = 12, the largest single instance: h = 2^-12 (4097 x 4097 nodes, 33.6M
   unknowns), y_D = +1 on [0.25, 0.75]^2, -1 elsewhere, plus U(-0.05, 0.05)
   noise (seed 5), alpha = 1e-6, LSGS.
@@ -35,7 +36,7 @@ from paper_1502_03917_gb300 import inputs  # noqa: E402
 WORKLOADS = {
     11: {"workload": "y_D = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1), seed 1; W(2,2) to h=1/2",
          "yd": lambda L: inputs.yd_sine_noise(L, 1),
-         "alphas": [1.0, 1e-2, 1e-4, 1e-6, 1e-8], "smoothers": ("lsgs", "ne")},
+         "alphas": [1.0, 1e-2, 1e-4, 1e-6, 1e-8], "smoothers": ("lsgs", "ne", "slsgs", "cgs")},
     12: {"workload": "y_D = +1 on [0.25,0.75]^2, -1 elsewhere, + U(-0.05,0.05), seed 5; W(2,2) to h=1/2",
          "yd": lambda L: inputs.yd_piecewise(L, 5),
          "alphas": [1e-6], "smoothers": ("lsgs",)},

@@ -4,7 +4,8 @@ oracle/make_golden.py, oracle only).
 
 * h = 2^-11 (2049 x 2049 nodes, 8.4M unknowns), the size the benchmark runs:
   y_D = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1) (seed 1), every alpha in
-  {1, 1e-2, 1e-4, 1e-6, 1e-8}, the LSGS and the NE smoother.
+  {1, 1e-2, 1e-4, 1e-6, 1e-8}, every smoother (LSGS, NE, sLSGS with 1+1
+  steps, CGS).
 * h = 2^-12 (4097 x 4097 nodes, 33.6M unknowns), the largest single instance:
   y_D = +-1 piecewise constant plus U(-0.05, 0.05) noise (seed 5),
   alpha = 1e-6, LSGS.
