@@ -176,6 +176,71 @@ struct StripEdges {
     }
 };
 
+// A thread's slot of the LSGS colour phases, resolved once per call.  The
+// slot index t of a phase enumerates the same kind of node for every colour:
+// a deep-interior node of row j, a node of a full edge row j, or a node of an
+// edge column i; only the position along that row or column depends on the
+// colour, through a residue mod 7:
+//   interior:  i = 2 + (c + m) mod 7 + 7k,  m = (-2 j - 2) mod 7
+//   edge row:  i =     (c + m) mod 7 + 7k,  m = (-2 j) mod 7
+//   edge col:  j = ja + (4c + m) mod 7 + 7k,  m = (-4 i - ja) mod 7
+// (colour of (i, j) = (i + 2j) mod 7, 4 = 2^-1 mod 7), so a phase costs a
+// few integer operations per slot instead of the enumeration (used by the
+// 513^2 kernel, whose threads have five slots per phase; in the one-slot
+// phases of the smaller levels it measured slower than the enumeration).
+// Packed into one int: kind (2 bits: 0 none, 1 interior, 2 edge row, 3 edge
+// column), m (3 bits), the fixed coordinate (11 bits: j for kinds 1, 2, i for
+// kind 3) and the base of the varying one (16 bits: 2 + 7k, 7k, ja + 7k).
+using SlotDesc = int;
+
+__device__ __forceinline__ int mod7(int v) { return ((v % 7) + 7) % 7; }
+
+__device__ __forceinline__ SlotDesc slot_pack(int kind, int m, int fixed, int base) {
+    return kind | (m << 2) | (fixed << 5) | (base << 16);
+}
+
+template <int N, int CPR>
+__device__ __forceinline__ SlotDesc slot_desc(int t, int ni, int nip, const StripEdges<N>& SE) {
+    if (t < nip) {
+        if (t >= ni) return 0;
+        const int r = t / CPR, k = t - r * CPR, j = SE.ja + r;
+        return slot_pack(1, mod7(-2 * j - 2), j, 2 + 7 * k);
+    }
+    t -= nip;
+    constexpr int FPR = StripEdges<N>::FPR;
+    if (t < SE.nfull * FPR) {
+        const int r = t / FPR, k = t - r * FPR;
+        const int j = r < SE.first_full_hi ? r : N - 1 + (r - SE.first_full_hi);
+        return slot_pack(2, mod7(-2 * j), j, 7 * k);
+    }
+    t -= SE.nfull * FPR;
+    const int pc = (SE.nrows + 6) / 7;
+    if (pc <= 0 || t >= 4 * pc) return 0;
+    const int q = t / pc, k = t - q * pc;
+    const int i = q < 2 ? q : N - 3 + q;
+    return slot_pack(3, mod7(-4 * i - SE.ja), i, SE.ja + 7 * k);
+}
+
+// the node of a slot in colour c; false if the slot is empty in this colour
+// (jmax: the last row of the strip's edge-column range)
+template <int N>
+__device__ __forceinline__ bool slot_node(SlotDesc d, int c, int jmax, int& i, int& j) {
+    const int kind = d & 3;
+    if (!kind) return false;
+    const int m = (d >> 2) & 7, fixed = (d >> 5) & 2047, base = d >> 16;
+    int r = (kind == 3 ? ((4 * c) % 7) : c) + m;
+    r -= r >= 7 ? 7 : 0;
+    const int pos = base + r;
+    if (kind == 3) {
+        i = fixed;
+        j = pos;
+        return pos <= jmax;
+    }
+    i = pos;
+    j = fixed;
+    return pos <= (kind == 1 ? N - 2 : N);
+}
+
 // ----------------------------------------------------------------- CGS --
 // Collective Gauss-Seidel update of node (i,j): the residual of its two rows
 // from the current iterate (x rows) and its (f_y, f_lambda), then the 2x2
@@ -447,8 +512,10 @@ __device__ __forceinline__ T rg_lsgs_edge(const LevelP<T>& P, const EdgeClass<T>
     return p;
 }
 
+constexpr int kRgThreads = 512;  // threads per block of the 513^2 cluster kernel
+
 template <typename T, int N>
-__global__ void __launch_bounds__(strip_threads<T>()) k_smooth_rg(LevelP<T> P, const EdgeClass<T>* __restrict__ ctab,
+__global__ void __launch_bounds__(kRgThreads) k_smooth_rg(LevelP<T> P, const EdgeClass<T>* __restrict__ ctab,
                                                                   int smoother, int steps, T* __restrict__ x,
                                                                   const T* __restrict__ f) {
     pdl_wait();
@@ -518,51 +585,50 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_rg(LevelP<T> P, c
     SE.nrows = nrows;
     (void)W;
 
-    // A thread's slots of a phase are handled kSlots at a time: first every
-    // slot's node and its x value (one round of L2 loads in flight together),
-    // then the updates.
-    constexpr int kSlots = 3;
+    // A thread's first kSlots slots of a phase are resolved once per call
+    // (SlotDesc); in a phase every slot's node and its x value come first (one
+    // round of L2 loads in flight together), then the updates.  Further slots
+    // (none at 513^2 with 16 blocks of 512 threads) by the enumeration.
+    constexpr int kSlots = 5;
+    const int ni = nrows * CPR, nip = (ni + 31) & ~31, ne = SE.count(0);
+    SlotDesc sd[kSlots];
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) sd[q] = slot_desc<N, CPR>(g + q * G, ni, nip, SE);
+    const int jmax = ja + nrows - 1;
     auto phase = [&](int field, int c) {
-        const int ni = nrows * CPR, nip = (ni + 31) & ~31;
-        const int ne = SE.count(c);
         const int64_t foff = field ? P.fs : 0;
-        for (int t0 = g; t0 < nip + ne; t0 += kSlots * G) {
-            int si[kSlots], sj[kSlots], kind[kSlots];  // kind 0: none, 1: interior, 2: edge
-            T xv[kSlots];
+        int si[kSlots], sj[kSlots];
+        bool on[kSlots];
+        T xv[kSlots];
 #pragma unroll
-            for (int q = 0; q < kSlots; ++q) {
-                const int t = t0 + q * G;
-                kind[q] = 0;
-                si[q] = sj[q] = 0;
-                if (t < nip) {
-                    if (t < ni) {
-                        const int r = t / CPR, k = t - r * CPR, j = ja + r;
-                        const int i = 2 + ((c - 2 * j - 2) % 7 + 7) % 7 + 7 * k;
-                        if (i <= N - 2) {
-                            kind[q] = 1;
-                            si[q] = i;
-                            sj[q] = j;
-                        }
-                    }
-                } else if (t < nip + ne) {
-                    int i, j;
-                    if (SE.node(t - nip, c, i, j)) {
-                        kind[q] = 2;
-                        si[q] = i;
-                        sj[q] = j;
-                    }
-                }
-                xv[q] = kind[q] ? x[(int64_t)sj[q] * LD + si[q] + foff] : T(0);
-            }
+        for (int q = 0; q < kSlots; ++q) {
+            on[q] = slot_node<N>(sd[q], c, jmax, si[q], sj[q]);
+            xv[q] = on[q] ? x[(int64_t)sj[q] * LD + si[q] + foff] : T(0);
+        }
 #pragma unroll
-            for (int q = 0; q < kSlots; ++q) {
-                if (!kind[q]) continue;
-                const int i = si[q], j = sj[q];
-                const T pv = kind[q] == 1
-                                 ? rg_lsgs_fast<T>(P, field, S.rrow(j), S.rrow(j + 1), S.rrow(j - 1), i)
-                                 : rg_lsgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], field, S, i, j);
-                x[(int64_t)j * LD + i + foff] = xv[q] + pv;
+        for (int q = 0; q < kSlots; ++q) {
+            if (!on[q]) continue;
+            const int i = si[q], j = sj[q];
+            const T pv = (sd[q] & 3) == 1
+                             ? rg_lsgs_fast<T>(P, field, S.rrow(j), S.rrow(j + 1), S.rrow(j - 1), i)
+                             : rg_lsgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], field, S, i, j);
+            x[(int64_t)j * LD + i + foff] = xv[q] + pv;
+        }
+        for (int t = g + kSlots * G; t < nip + ne; t += G) {
+            int i, j;
+            T pv;
+            if (t < nip) {
+                if (t >= ni) continue;
+                const int r = t / CPR, k = t - r * CPR;
+                j = ja + r;
+                i = 2 + ((c - 2 * j - 2) % 7 + 7) % 7 + 7 * k;
+                if (i > N - 2) continue;
+                pv = rg_lsgs_fast<T>(P, field, S.rrow(j), S.rrow(j + 1), S.rrow(j - 1), i);
+            } else {
+                if (!SE.node(t - nip, c, i, j)) continue;
+                pv = rg_lsgs_edge<T, N>(P, s_cls[cls5(i, N) + 5 * cls5(j, N)], field, S, i, j);
             }
+            x[(int64_t)j * LD + i + foff] += pv;
         }
         cluster_barrier();
     };
@@ -706,7 +772,7 @@ template <typename T>
 cudaLaunchConfig_t rg_config(cudaStream_t s, cudaLaunchAttribute* at, bool pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kRgBlocks, 1, 1);
-    cfg.blockDim = dim3(strip_threads<T>(), 1, 1);
+    cfg.blockDim = dim3(kRgThreads, 1, 1);
     cfg.dynamicSmemBytes = rg_smem<T>();
     cfg.stream = s;
     cfg.attrs = at;
