@@ -68,3 +68,35 @@ def batch_instances(count: int, seed: int, lmin: int = 6, lmax: int = 10):
     alphas = 10.0 ** rng.uniform(-8.0, 0.0, size=count)
     yds = [rng.uniform(-1.0, 1.0, ((1 << int(L)) + 1) ** 2) for L in levels]
     return [int(L) for L in levels], [float(a) for a in alphas], yds
+
+
+# ---------------------------------------------------------------- Stokes --
+# Stokes control unknowns of level L (n = 2^L cells per side):
+# x = (v_1, v_2, p, lambda_1, lambda_2, mu); velocities on the (2n-1)^2
+# interior nodes of the half-step grid, pressures on the (n+1)^2 vertices.
+
+
+def stokes_sizes(L: int) -> tuple[int, int, int]:
+    """(unknowns per velocity component, pressure vertices, all unknowns)."""
+    n = 1 << L
+    nv, npn = (2 * n - 1) ** 2, (n + 1) ** 2
+    return nv, npn, 4 * nv + 2 * npn
+
+
+def stokes_x_uniform(L: int, seed: int) -> np.ndarray:
+    """A random Stokes iterate, every unknown i.i.d. U(-1, 1)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, stokes_sizes(L)[2])
+
+
+def stokes_vd_vortex(L: int, seed: int) -> np.ndarray:
+    """Desired velocity at all (2n+1)^2 nodes of the half-step grid (component
+    major): the divergence-free vortex v_D = curl of sin(pi x)^2 sin(pi y)^2,
+    plus 0.1 N(0, 1) noise per component."""
+    n = 1 << L
+    t = np.arange(2 * n + 1, dtype=np.float64) / (2 * n)
+    X, Y = (a.ravel() for a in np.meshgrid(t, t, indexing="xy"))
+    sx, sy = np.sin(np.pi * X), np.sin(np.pi * Y)
+    u = 2 * np.pi * sx * sx * sy * np.cos(np.pi * Y)
+    v = -2 * np.pi * sy * sy * sx * np.cos(np.pi * X)
+    noise = 0.1 * np.random.default_rng(seed).standard_normal(2 * X.size)
+    return np.concatenate([u, v]) + noise

@@ -19,3 +19,11 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def stokes_mod():
+    from oracle import stokes
+
+    stokes.build()
+    return stokes
