@@ -31,6 +31,13 @@ int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
+}  // namespace
+
+namespace aaomg {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace aaomg
+
+namespace {
 
 #define CK(call)                                                                                    \
     do {                                                                                            \
