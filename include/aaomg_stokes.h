@@ -70,13 +70,20 @@ typedef struct {
     int max_iter;  /* ms_solve iteration cap; <= 0: 100 */
     int block_max; /* levels up to this one smooth in one single-block launch per smoothing call
                       (iterate and residual in shared memory; at most 4); < 0: none; 0: 4 */
+    int dense_level; /* the coarse-grid correction of this level (the gamma iterations of the levels
+                        up to it, from zero) is applied as one dense linear map, built at set-up by
+                        running those iterations on every unit vector: the same iterate up to
+                        rounding, without the latency of the coarse levels' colour phases.  1..5
+                        (below levels); 0: 5 when levels >= 7, 4 when levels is 5 or 6, else
+                        none; < 0: none */
 } ms_options;
 
 /* Build the hierarchy for h = 2^-levels (1 <= levels <= 9; level 1, h = 1/2,
  * has 54 unknowns) and alpha > 0 (finite): assembles M, K and D of every level,
- * A, L and N_ii = sum_j A_ji^2 / L_jj (Algorithm 2), the embeddings, and the
- * coarsest solution operator; allocates the device workspaces on the current
- * device.  opt may be NULL (defaults).  Errors: BAD_ARG, NO_DEVICE, OOM, CUDA. */
+ * A, L and N_ii = sum_j A_ji^2 / L_jj (Algorithm 2), the embeddings, the
+ * coarsest solution operator and the dense coarse-level map; allocates the
+ * device workspaces on the current device (the level-5 map holds 2.6 GB).  opt
+ * may be NULL (defaults).  Errors: BAD_ARG, NO_DEVICE, OOM, CUDA. */
 AAOMG_API int ms_setup(int levels, double alpha, const ms_options* opt, ms_handle* out);
 
 /* Free a handle (NULL is ignored).  Synchronises the device. */

@@ -2,25 +2,30 @@
 // discretisation of the optimality system of eq. (mp3), assembled on the host,
 // and its all-at-once multigrid iteration (section 2) on the GPU in FP64.
 //
-// Storage.  Every level keeps A in a sliced ELL format (slices of 32 rows, each
-// slice as wide as its longest row, entries of a slice stored slot by slot so
-// that the 32 threads of a warp read consecutive words) with the rows in the
-// LSGS visiting order: block by block (v_1, v_2, p, lambda_1, lambda_2, mu),
-// colour by colour, each colour padded to whole slices and sorted by row
-// length inside (vertex nodes of the P2 grid have 45 entries, edge nodes 22,
-// pressure rows 38), so that a warp mostly runs rows of one length.  Beside
-// A_ij the slice holds A_ij / L_jj, the weight of the gather of Algorithm 2.
+// Storage.  Every level keeps A with its rows in the LSGS visiting order:
+// block by block (v_1, v_2, p, lambda_1, lambda_2, mu), colour by colour, each
+// colour padded to whole warps and sorted by row length inside (vertex nodes
+// of the P2 grid have 45 entries, edge nodes 22, pressure rows 38).  A row's
+// entries (column, A_ij and A_ij / L_jj, the weight of the gather of
+// Algorithm 2) are contiguous, their count padded to a multiple of 8, and 8
+// lanes of a warp share a row, so that the lanes read consecutive words.
 // Vectors stay in the natural block order of the ABI.
 //
 // Kernels.  A colour of LSGS is one launch over its rows (gather q = sum_j
 // A_ij r_j / L_jj, p = q / N_ii, x_i += p, scatter r_j -= A_ji p; the rows of a
-// colour touch disjoint entries of r, so the updates of a launch commute); on
-// levels up to 4 (at most 4422 unknowns) a whole smoothing call runs in one
-// single-block launch with x and r in shared memory and a barrier between
-// colours.  Residual, restriction (the transposes of the embeddings) and
-// prolongation are row-parallel kernels over CSR matrices; the coarsest level
-// applies a precomputed dense solution operator.  One cycle is recorded once
-// into a CUDA graph.
+// colour touch disjoint entries of r, so the updates of a launch commute and
+// each row's scatter reuses the values its gather loaded); on levels up to 4
+// (at most 4422 unknowns) a whole smoothing call runs in one single-block
+// launch with x and r in shared memory and a barrier between colours.
+// Residual, restriction (the transposes of the embeddings) and prolongation are
+// row-parallel kernels over CSR matrices; the coarsest level applies a
+// precomputed dense solution operator.  The coarse-grid correction of level 5
+// or 4 (the gamma iterations of all coarser levels from zero, a fixed linear
+// map of the restricted defect) is applied as one dense matrix built at
+// set-up by running those iterations on every unit vector (multi-vector forms
+// of the same kernels), so the cycle does not pay the colour phases' launch
+// latency on the coarse levels.  Launches use programmatic dependent launch;
+// one cycle is recorded once into a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,12 +37,15 @@
 
 #include "aaomg_stokes.h"
 #include "errors.h"
+#include "pdl.h"
 #include "trace.h"
 
 namespace {
 
 using aaomg::set_error;
 using aaomg::TraceRange;
+using aaomg::launch_pdl;
+using aaomg::pdl_wait;
 
 #define SCK(call)                                                                                        \
     do {                                                                                                 \
@@ -46,127 +54,188 @@ using aaomg::TraceRange;
             return set_error(AAOMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
     } while (0)
 
-constexpr int kSlice = 32;
+constexpr int kGroup = 8;  // lanes per row of A
 constexpr int kVCol = 19;  // colours (a + 7 b) mod 19 of the P2 half-step grid
 constexpr int kPCol = 7;   // colours (i + 2 j) mod 7 of the vertices
 constexpr int kSmallThreads = 1024;
 constexpr int kNormBlocks = 296;
+constexpr int kMaxPerLane = 6;  // entries of the longest row (45) per lane, rounded up
 
 // ============================================================ kernels ==
 
-struct SellDev {
-    int m;                  // unknowns
-    int nrows;              // padded rows (a multiple of kSlice)
-    const int* rowid;       // natural index of each padded row, -1 for padding
-    const int* len;         // entries of each padded row
-    const long long* sptr;  // start of each slice
-    const int* col;         // natural column of each entry
-    const double* a;        // A_ij
-    const double* al;       // A_ij / L_jj
-    const double* invN;     // 1 / N_ii per padded row
-    const double* invL;     // 1 / L_ii, natural order
+// A in the LSGS visiting order: row `row` holds the entries [start, start +
+// len) of col / a / al, its length padded to a multiple of kGroup (padding:
+// column 0, weight 0).  Rows are padded per colour to whole warps (rowid -1).
+struct RowsDev {
+    int m;                   // unknowns
+    int nrows;               // rows in the visiting order, padding included
+    const int* rowid;        // natural index of each row, -1 for padding
+    const int* len;          // padded length of each row
+    const long long* start;  // first entry of each row
+    const int* col;          // natural column of each entry
+    const double* a;         // A_ij
+    const double* al;        // A_ij / L_jj
+    const double* invN;      // 1 / N_ii per row
+    const double* invL;      // 1 / L_ii, natural order
 };
 
-__device__ __forceinline__ long long sell_at(const SellDev& S, int row, int k) {
-    return S.sptr[row / kSlice] + (long long)k * kSlice + (row % kSlice);
+// The kGroup lanes of a group (aligned within a warp) share one row: lane l
+// takes the entries l, l + kGroup, ...; all its loads are issued before their
+// first use, the partial sums meet by shuffles.  Every lane of the group gets
+// the row's sum; row < 0: zero (every lane of the warp still takes part in the
+// shuffles).
+__device__ __forceinline__ double group_dot(const RowsDev& S, int row, int lane, const double* v, const double* w) {
+    double acc = 0.0;
+    if (row >= 0) {
+        const int n = S.len[row];
+        const long long b = S.start[row] + lane;
+        int c[kMaxPerLane];
+        double wk[kMaxPerLane];
+#pragma unroll
+        for (int u = 0; u < kMaxPerLane; ++u) {
+            const bool on = lane + u * kGroup < n;
+            c[u] = on ? S.col[b + u * kGroup] : 0;
+            wk[u] = on ? w[b + u * kGroup] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kMaxPerLane; ++u) acc += wk[u] * v[c[u]];
+    }
+#pragma unroll
+    for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kGroup);
+    return acc;
 }
 
-// one row of Algorithm 2 on (x, r) (global or shared memory)
-__device__ __forceinline__ void lsgs_row(const SellDev& S, int row, double* x, double* r) {
-    const int i = S.rowid[row];
+// one row of Algorithm 2 on (x, r) (global or shared memory) by a group:
+// gather q = sum_j A_ij r_j / L_jj, p = q / N_ii, x_i += p, scatter
+// r_j -= A_ji p (A symmetric: the row's own entries).  No other row of the
+// colour touches these r_j, so the scatter reuses the gathered values and
+// indices: every load of the row is issued at the start.  row < 0 or a
+// padding row: shuffles only.
+__device__ __forceinline__ void group_lsgs(const RowsDev& S, int row, int lane, double* x, double* r) {
+    const int i = row >= 0 ? S.rowid[row] : -1;
+    int c[kMaxPerLane];
+    double wl[kMaxPerLane], ak[kMaxPerLane], rk[kMaxPerLane];
+    double acc = 0.0;
+    if (i >= 0) {
+        const int n = S.len[row];
+        const long long b = S.start[row] + lane;
+#pragma unroll
+        for (int u = 0; u < kMaxPerLane; ++u) {
+            const bool on = lane + u * kGroup < n;
+            c[u] = on ? S.col[b + u * kGroup] : -1;
+            wl[u] = on ? S.al[b + u * kGroup] : 0.0;
+            ak[u] = on ? S.a[b + u * kGroup] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kMaxPerLane; ++u) rk[u] = c[u] >= 0 ? r[c[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kMaxPerLane; ++u) acc += wl[u] * rk[u];
+    }
+#pragma unroll
+    for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kGroup);
     if (i < 0) return;
-    const int n = S.len[row];
-    const long long b = sell_at(S, row, 0);
-    double q0 = 0.0, q1 = 0.0;
-    int k = 0;
-    for (; k + 1 < n; k += 2) {
-        q0 += S.al[b + (long long)k * kSlice] * r[S.col[b + (long long)k * kSlice]];
-        q1 += S.al[b + (long long)(k + 1) * kSlice] * r[S.col[b + (long long)(k + 1) * kSlice]];
-    }
-    if (k < n) q0 += S.al[b + (long long)k * kSlice] * r[S.col[b + (long long)k * kSlice]];
-    const double p = (q0 + q1) * S.invN[row];
-    x[i] += p;
-    for (k = 0; k < n; ++k) {
-        const long long e = b + (long long)k * kSlice;
-        r[S.col[e]] -= S.a[e] * p;
-    }
+    const double p = acc * S.invN[row];
+    if (lane == 0) x[i] += p;
+#pragma unroll
+    for (int u = 0; u < kMaxPerLane; ++u)
+        if (c[u] >= 0 && ak[u] != 0.0) r[c[u]] = rk[u] - ak[u] * p;
 }
 
-__device__ __forceinline__ double row_dot(const SellDev& S, int row, const double* v, const double* al_or_a) {
-    const int n = S.len[row];
-    const long long b = sell_at(S, row, 0);
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) {
-        const long long e = b + (long long)k * kSlice;
-        s += al_or_a[e] * v[S.col[e]];
-    }
-    return s;
-}
-
-__global__ void k_st_phase(SellDev S, int r0, int cnt, double* x, double* r) {
+// the rows [r0, r0 + cnt) of one colour, a group per row; vector blockIdx.y
+// of multi-vectors at stride m
+__global__ void k_st_phase(RowsDev S, int r0, int cnt, double* x, double* r) {
+    pdl_wait();
+    x += (size_t)blockIdx.y * S.m;
+    r += (size_t)blockIdx.y * S.m;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < cnt) lsgs_row(S, r0 + t, x, r);
+    const int g = t / kGroup, lane = t % kGroup;
+    group_lsgs(S, g < cnt ? r0 + g : -1, lane, x, r);
 }
 
 // r = f - A x over all rows
-__global__ void k_st_resid(SellDev S, const double* f, const double* x, double* r) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= S.nrows) return;
-    const int i = S.rowid[row];
-    if (i < 0) return;
-    r[i] = f[i] - row_dot(S, row, x, S.a);
+__global__ void k_st_resid(RowsDev S, const double* f, const double* x, double* r) {
+    pdl_wait();
+    const size_t vo = (size_t)blockIdx.y * S.m;
+    f += vo;
+    x += vo;
+    r += vo;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = t / kGroup, lane = t % kGroup;
+    const int i = row < S.nrows ? S.rowid[row] : -1;
+    const double s = group_dot(S, i >= 0 ? row : -1, lane, x, S.a);
+    if (i >= 0 && lane == 0) r[i] = f[i] - s;
 }
 
 // Algorithm 1, first loop: p_i = tau (sum_j A_ij r_j / L_jj) / L_ii
-__global__ void k_st_ne_p(SellDev S, double tau, const double* r, double* p) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= S.nrows) return;
-    const int i = S.rowid[row];
-    if (i < 0) return;
-    p[i] = tau * row_dot(S, row, r, S.al) * S.invL[i];
+__global__ void k_st_ne_p(RowsDev S, double tau, const double* r, double* p) {
+    pdl_wait();
+    const size_t vo = (size_t)blockIdx.y * S.m;
+    r += vo;
+    p += vo;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = t / kGroup, lane = t % kGroup;
+    const int i = row < S.nrows ? S.rowid[row] : -1;
+    const double q = group_dot(S, i >= 0 ? row : -1, lane, r, S.al);
+    if (i >= 0 && lane == 0) p[i] = tau * q * S.invL[i];
 }
 
 // Algorithm 1, second loop (gather form, A symmetric): x_i += p_i,
 // r_i -= sum_j A_ij p_j
-__global__ void k_st_ne_update(SellDev S, const double* p, double* x, double* r) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= S.nrows) return;
-    const int i = S.rowid[row];
-    if (i < 0) return;
-    x[i] += p[i];
-    r[i] -= row_dot(S, row, p, S.a);
+__global__ void k_st_ne_update(RowsDev S, const double* p, double* x, double* r) {
+    pdl_wait();
+    const size_t vo = (size_t)blockIdx.y * S.m;
+    p += vo;
+    x += vo;
+    r += vo;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = t / kGroup, lane = t % kGroup;
+    const int i = row < S.nrows ? S.rowid[row] : -1;
+    const double s = group_dot(S, i >= 0 ? row : -1, lane, p, S.a);
+    if (i >= 0 && lane == 0) {
+        x[i] += p[i];
+        r[i] -= s;
+    }
 }
 
 // A whole smoothing call on a small level in one block: x and r (and the NE
-// update p) in shared memory, a barrier between dependent passes.  smoother:
-// 0 NE, 1 LSGS, 2 sLSGS.
+// update p) in shared memory, a barrier between dependent passes, a group of
+// kGroup lanes per row; block b works on vector b of a multi-vector.
+// smoother: 0 NE, 1 LSGS, 2 sLSGS.
 __global__ void __launch_bounds__(kSmallThreads)
-    k_st_small(SellDev S, const int* __restrict__ poff, int nph, int smoother, int steps, double tau,
+    k_st_small(RowsDev S, const int* __restrict__ poff, int nph, int smoother, int steps, double tau,
                const double* __restrict__ f, double* __restrict__ x) {
+    pdl_wait();
     extern __shared__ double sm[];
     double* xs = sm;
     double* rs = sm + S.m;
     double* ps = sm + 2 * S.m;
+    f += (size_t)blockIdx.x * S.m;
+    x += (size_t)blockIdx.x * S.m;
     const int g = threadIdx.x, G = blockDim.x;
+    const int grp = g / kGroup, lane = g % kGroup, NG = G / kGroup;
+    const int nrow_pad = (S.nrows + NG - 1) / NG * NG;  // whole rounds: every group meets the shuffles
     for (int i = g; i < S.m; i += G) xs[i] = x[i];
     __syncthreads();
-    for (int row = g; row < S.nrows; row += G) {
-        const int i = S.rowid[row];
-        if (i >= 0) rs[i] = f[i] - row_dot(S, row, xs, S.a);
+    for (int row = grp; row < nrow_pad; row += NG) {
+        const int i = row < S.nrows ? S.rowid[row] : -1;
+        const double s = group_dot(S, i >= 0 ? row : -1, lane, xs, S.a);
+        if (i >= 0 && lane == 0) rs[i] = f[i] - s;
     }
     __syncthreads();
     for (int m = 0; m < steps; ++m) {
         if (smoother == 0) {
-            for (int row = g; row < S.nrows; row += G) {
-                const int i = S.rowid[row];
-                if (i >= 0) ps[i] = tau * row_dot(S, row, rs, S.al) * S.invL[i];
+            for (int row = grp; row < nrow_pad; row += NG) {
+                const int i = row < S.nrows ? S.rowid[row] : -1;
+                const double q = group_dot(S, i >= 0 ? row : -1, lane, rs, S.al);
+                if (i >= 0 && lane == 0) ps[i] = tau * q * S.invL[i];
             }
             __syncthreads();
-            for (int row = g; row < S.nrows; row += G) {
-                const int i = S.rowid[row];
-                if (i >= 0) {
+            for (int row = grp; row < nrow_pad; row += NG) {
+                const int i = row < S.nrows ? S.rowid[row] : -1;
+                const double s = group_dot(S, i >= 0 ? row : -1, lane, ps, S.a);
+                if (i >= 0 && lane == 0) {
                     xs[i] += ps[i];
-                    rs[i] -= row_dot(S, row, ps, S.a);
+                    rs[i] -= s;
                 }
             }
             __syncthreads();
@@ -175,8 +244,9 @@ __global__ void __launch_bounds__(kSmallThreads)
         for (int pass = 0; pass < (smoother == 2 ? 2 : 1); ++pass)
             for (int q = 0; q < nph; ++q) {
                 const int ph = pass == 0 ? q : nph - 1 - q;
-                const int r0 = poff[ph], r1 = poff[ph + 1];
-                for (int row = r0 + g; row < r1; row += G) lsgs_row(S, row, xs, rs);
+                const int r0 = poff[ph], cnt = poff[ph + 1] - r0;
+                const int cnt_pad = (cnt + NG - 1) / NG * NG;
+                for (int k = grp; k < cnt_pad; k += NG) group_lsgs(S, k < cnt ? r0 + k : -1, lane, xs, rs);
                 __syncthreads();
             }
     }
@@ -219,8 +289,12 @@ __device__ __forceinline__ void locate(const Blocks& B, int u, int& blk, int& j)
 // fc = I^T rf, block by block: R2 = P2^T on velocities, R1 = P1^T on pressures
 __global__ void k_st_restrict(Blocks Bf, Blocks Bc, CsrDev R2, CsrDev R1, const double* __restrict__ rf,
                               double* __restrict__ fc, double* __restrict__ xc) {
+    pdl_wait();
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= Bc.m()) return;
+    rf += (size_t)blockIdx.y * Bf.m();  // vector blockIdx.y of multi-vectors
+    fc += (size_t)blockIdx.y * Bc.m();
+    xc += (size_t)blockIdx.y * Bc.m();
     int blk, j;
     locate(Bc, u, blk, j);
     const CsrDev& R = Bc.vel(blk) ? R2 : R1;
@@ -234,8 +308,11 @@ __global__ void k_st_restrict(Blocks Bf, Blocks Bc, CsrDev R2, CsrDev R1, const 
 // xf += I xc, block by block
 __global__ void k_st_prolong(Blocks Bf, Blocks Bc, CsrDev P2, CsrDev P1, const double* __restrict__ xc,
                              double* __restrict__ xf) {
+    pdl_wait();
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= Bf.m()) return;
+    xc += (size_t)blockIdx.y * Bc.m();
+    xf += (size_t)blockIdx.y * Bf.m();
     int blk, j;
     locate(Bf, u, blk, j);
     const CsrDev& P = Bf.vel(blk) ? P2 : P1;
@@ -245,8 +322,12 @@ __global__ void k_st_prolong(Blocks Bf, Blocks Bc, CsrDev P2, CsrDev P1, const d
     xf[u] += s;
 }
 
-// coarsest level: x = G f (G the solution operator with int p = int mu = 0)
+// coarsest level: x = G f (G the solution operator with int p = int mu = 0);
+// block b solves for vector b of a multi-vector
 __global__ void k_st_coarse(int m, const double* __restrict__ G, const double* __restrict__ f, double* __restrict__ x) {
+    pdl_wait();
+    f += (size_t)blockIdx.x * m;
+    x += (size_t)blockIdx.x * m;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double s = 0.0;
         for (int j = 0; j < m; ++j) s += G[(size_t)i * m + j] * f[j];
@@ -254,8 +335,45 @@ __global__ void k_st_coarse(int m, const double* __restrict__ G, const double* _
     }
 }
 
+// x = B f with the dense map B of the coarse levels (column-major, m x m):
+// block (bx, by) sums the columns [by ck, (by + 1) ck) for the rows of tile bx
+// into part[by]; k_st_dense_sum adds the partial sums in a fixed order
+constexpr int kDenseChunks = 32;
+__global__ void k_st_dense(int m, int ck, const double* __restrict__ B, const double* __restrict__ f,
+                           double* __restrict__ part) {
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int j0 = blockIdx.y * ck, j1 = min(m, j0 + ck);
+    double s0 = 0.0, s1 = 0.0;
+    int j = j0;
+    for (; j + 1 < j1; j += 2) {
+        s0 += B[(size_t)j * m + i] * f[j];
+        s1 += B[(size_t)(j + 1) * m + i] * f[j + 1];
+    }
+    if (j < j1) s0 += B[(size_t)j * m + i] * f[j];
+    part[(size_t)blockIdx.y * m + i] = s0 + s1;
+}
+
+__global__ void k_st_dense_sum(int m, const double* __restrict__ part, double* __restrict__ x) {
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double s = 0.0;
+    for (int c = 0; c < kDenseChunks; ++c) s += part[(size_t)c * m + i];
+    x[i] = s;
+}
+
+// the unit vectors e_{j0} .. e_{j0 + nc - 1} of R^m as a multi-vector
+__global__ void k_st_identity(int m, int j0, int nc, double* __restrict__ e) {
+    pdl_wait();
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (size_t)m * nc) e[t] = ((size_t)j0 + t / m == t % m) ? 1.0 : 0.0;
+}
+
 // f = (M v_D, 0, 0, 0): Mf holds the interior rows of the full P2 mass matrix
 __global__ void k_st_rhs(Blocks B, int ng2, CsrDev Mf, const double* __restrict__ vD, double* __restrict__ f) {
+    pdl_wait();
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= B.m()) return;
     double s = 0.0;
@@ -282,6 +400,7 @@ __device__ __forceinline__ double block_sum(double v) {
 // the means of p and mu: out[0] = sum_q w_q p_q, out[1] = sum_q w_q mu_q
 // (sum_q w_q = |Omega| = 1); one block
 __global__ void k_st_means(Blocks B, const double* __restrict__ w, const double* __restrict__ x, double* out) {
+    pdl_wait();
     double sp = 0.0, sm = 0.0;
     for (int q = threadIdx.x; q < B.np; q += blockDim.x) {
         sp += w[q] * x[B.off(2) + q];
@@ -296,6 +415,7 @@ __global__ void k_st_means(Blocks B, const double* __restrict__ w, const double*
 }
 
 __global__ void k_st_shift(Blocks B, const double* __restrict__ means, double* __restrict__ x) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= B.np) return;
     x[B.off(2) + q] -= means[0];
@@ -308,6 +428,7 @@ __global__ void k_st_shift(Blocks B, const double* __restrict__ means, double* _
 // (means may be null: no shift)
 __global__ void k_st_norm_part(Blocks B, int mode, const double* __restrict__ invL, const double* __restrict__ v,
                                const double* __restrict__ g, const double* __restrict__ means, double* part) {
+    pdl_wait();
     double s0 = 0.0, s1 = 0.0;
     const int m = B.m();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -333,6 +454,7 @@ __global__ void k_st_norm_part(Blocks B, int mode, const double* __restrict__ in
 }
 
 __global__ void k_st_norm_final(const double* __restrict__ part, int nblk, double* out) {
+    pdl_wait();
     double s0 = 0.0, s1 = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         s0 += part[2 * b];
@@ -718,7 +840,7 @@ struct ms_ctx {
         int n = 0, nv = 0, np = 0, m = 0, nrows = 0, nph = 0;
         std::vector<int> poff;  // phase offsets into the padded rows (host)
         int *rowid = nullptr, *len = nullptr, *col = nullptr, *poff_d = nullptr;
-        long long* sptr = nullptr;
+        long long* start = nullptr;
         double *a = nullptr, *al = nullptr, *invN = nullptr, *invL = nullptr, *w = nullptr;
         // embeddings from the next coarser level (P2, P1) and their transposes
         int *p2p = nullptr, *p2c = nullptr, *p1p = nullptr, *p1c = nullptr;
@@ -726,14 +848,17 @@ struct ms_ctx {
         double *p2v = nullptr, *p1v = nullptr, *r2v = nullptr, *r1v = nullptr;
         double *x = nullptr, *f = nullptr, *r = nullptr, *p = nullptr;
         bool small = false;
-        SellDev sell() const {
-            return SellDev{m, nrows, rowid, len, sptr, col, a, al, invN, invL};
+        RowsDev rows() const {
+            return RowsDev{m, nrows, rowid, len, start, col, a, al, invN, invL};
         }
         Blocks blocks() const { return Blocks{nv, np}; }
     };
     int L = 0;
     double alpha = 0.0;
     ms_options o{};
+    int kd = 0;               // levels <= kd are replaced by their dense map (0: none)
+    double* B = nullptr;      // the dense map on level kd, column-major
+    double* dpart = nullptr;  // its partial sums
     int device = 0;
     std::vector<Lev> lev;  // 1..L
     double* G = nullptr;   // coarsest solution operator
@@ -814,41 +939,35 @@ int build_level(ms_ctx* H, const HostLevel& HL, ms_ctx::Lev& D) {
     D.poff.assign(1, 0);
     for (const auto& c : cls) {
         for (int u : c) rowid.push_back(u);
-        while (rowid.size() % kSlice) rowid.push_back(-1);
+        while (rowid.size() % 4) rowid.push_back(-1);  // four rows of kGroup lanes per warp
         D.poff.push_back((int)rowid.size());
     }
     D.nph = (int)cls.size();
     D.nrows = (int)rowid.size();
-    const int nsl = D.nrows / kSlice;
     std::vector<int> len(D.nrows, 0);
-    std::vector<long long> sptr(nsl + 1, 0);
-    for (int s = 0; s < nsl; ++s) {
-        int wmax = 0;
-        for (int k = 0; k < kSlice; ++k) {
-            const int u = rowid[s * kSlice + k];
-            len[s * kSlice + k] = u < 0 ? 0 : rowlen[u];
-            wmax = std::max(wmax, len[s * kSlice + k]);
-        }
-        sptr[s + 1] = sptr[s] + (long long)wmax * kSlice;
+    std::vector<long long> start(D.nrows + 1, 0);
+    for (int row = 0; row < D.nrows; ++row) {
+        const int u = rowid[row];
+        len[row] = u < 0 ? 0 : (rowlen[u] + kGroup - 1) / kGroup * kGroup;
+        start[row + 1] = start[row] + len[row];
     }
-    const size_t ne = (size_t)sptr[nsl];
+    const size_t ne = (size_t)start[D.nrows];
     std::vector<int> col(ne, 0);
     std::vector<double> a(ne, 0.0), al(ne, 0.0), invN(D.nrows, 0.0);
     for (int row = 0; row < D.nrows; ++row) {
         const int u = rowid[row];
         if (u < 0) continue;
         invN[row] = 1.0 / Nd[u];
-        const long long b = sptr[row / kSlice] + row % kSlice;
         a_row(HL, H->alpha, u, rc, rv);
         for (int k = 0; k < rowlen[u]; ++k) {
-            col[b + (long long)k * kSlice] = rc[k];
-            a[b + (long long)k * kSlice] = rv[k];
-            al[b + (long long)k * kSlice] = rv[k] / HL.Ld[rc[k]];
+            col[start[row] + k] = rc[k];
+            a[start[row] + k] = rv[k];
+            al[start[row] + k] = rv[k] / HL.Ld[rc[k]];
         }
     }
     int rc_;
     if ((rc_ = dev_upload(H, D.rowid, rowid.data(), rowid.size())) || (rc_ = dev_upload(H, D.len, len.data(), len.size())) ||
-        (rc_ = dev_upload(H, D.sptr, sptr.data(), sptr.size())) || (rc_ = dev_upload(H, D.col, col.data(), col.size())) ||
+        (rc_ = dev_upload(H, D.start, start.data(), start.size())) || (rc_ = dev_upload(H, D.col, col.data(), col.size())) ||
         (rc_ = dev_upload(H, D.a, a.data(), a.size())) || (rc_ = dev_upload(H, D.al, al.data(), al.size())) ||
         (rc_ = dev_upload(H, D.invN, invN.data(), invN.size())) ||
         (rc_ = dev_upload(H, D.invL, invL.data(), invL.size())) ||
@@ -892,20 +1011,21 @@ int grid_of(long long n, int t = 256) { return (int)((n + t - 1) / t); }
 
 void launch_smooth(ms_ctx* H, int k, const double* f, double* x, int steps, cudaStream_t s) {
     ms_ctx::Lev& D = H->lev[k];
-    const SellDev S = D.sell();
+    const RowsDev S = D.rows();
     const int sm = H->o.smoother;
     if (D.small) {
-        k_st_small<<<1, kSmallThreads, 3 * (size_t)D.m * sizeof(double), s>>>(S, D.poff_d, D.nph, sm, steps,
-                                                                                H->o.tau, f, x);
+        launch_pdl(k_st_small, dim3(1), dim3(kSmallThreads), 3 * (size_t)D.m * sizeof(double), s, S,
+                   (const int*)D.poff_d, D.nph, sm, steps, H->o.tau, f, x);
         ++H->launches;
         return;
     }
-    k_st_resid<<<grid_of(D.nrows), 256, 0, s>>>(S, f, x, D.r);
+    const int gr = grid_of((long long)D.nrows * kGroup);
+    launch_pdl(k_st_resid, dim3(gr), dim3(256), 0, s, S, f, (const double*)x, D.r);
     ++H->launches;
     for (int m = 0; m < steps; ++m) {
         if (sm == MS_SMOOTHER_NE) {
-            k_st_ne_p<<<grid_of(D.nrows), 256, 0, s>>>(S, H->o.tau, D.r, D.p);
-            k_st_ne_update<<<grid_of(D.nrows), 256, 0, s>>>(S, D.p, x, D.r);
+            launch_pdl(k_st_ne_p, dim3(gr), dim3(256), 0, s, S, H->o.tau, (const double*)D.r, D.p);
+            launch_pdl(k_st_ne_update, dim3(gr), dim3(256), 0, s, S, (const double*)D.p, x, D.r);
             H->launches += 2;
             continue;
         }
@@ -914,7 +1034,7 @@ void launch_smooth(ms_ctx* H, int k, const double* f, double* x, int steps, cuda
                 const int ph = pass == 0 ? q : D.nph - 1 - q;
                 const int r0 = D.poff[ph], cnt = D.poff[ph + 1] - r0;
                 if (cnt == 0) continue;
-                k_st_phase<<<grid_of(cnt, 128), 128, 0, s>>>(S, r0, cnt, x, D.r);
+                launch_pdl(k_st_phase, dim3(grid_of((long long)cnt * kGroup)), dim3(256), 0, s, S, r0, cnt, x, D.r);
                 ++H->launches;
             }
     }
@@ -922,13 +1042,13 @@ void launch_smooth(ms_ctx* H, int k, const double* f, double* x, int steps, cuda
 
 void launch_resid(ms_ctx* H, int k, const double* f, const double* x, double* r, cudaStream_t s) {
     ms_ctx::Lev& D = H->lev[k];
-    k_st_resid<<<grid_of(D.nrows), 256, 0, s>>>(D.sell(), f, x, r);
+    launch_pdl(k_st_resid, dim3(grid_of((long long)D.nrows * kGroup)), dim3(256), 0, s, D.rows(), f, x, r);
     ++H->launches;
 }
 
 void cycle_rec(ms_ctx* H, int k, const double* f, double* x, cudaStream_t s) {
     if (k == 1) {
-        k_st_coarse<<<1, 256, 0, s>>>(H->lev[1].m, H->G, f, x);
+        launch_pdl(k_st_coarse, dim3(1), dim3(256), 0, s, H->lev[1].m, (const double*)H->G, f, x);
         ++H->launches;
         return;
     }
@@ -936,14 +1056,122 @@ void cycle_rec(ms_ctx* H, int k, const double* f, double* x, cudaStream_t s) {
     ms_ctx::Lev& C = H->lev[k - 1];
     if (H->o.nu_pre > 0) launch_smooth(H, k, f, x, H->o.nu_pre, s);
     launch_resid(H, k, f, x, D.r, s);
-    k_st_restrict<<<grid_of(C.m), 256, 0, s>>>(D.blocks(), C.blocks(), CsrDev{D.r2p, D.r2c, D.r2v},
-                                               CsrDev{D.r1p, D.r1c, D.r1v}, D.r, C.f, C.x);
+    launch_pdl(k_st_restrict, dim3(grid_of(C.m)), dim3(256), 0, s, D.blocks(), C.blocks(),
+               CsrDev{D.r2p, D.r2c, D.r2v}, CsrDev{D.r1p, D.r1c, D.r1v}, (const double*)D.r, C.f, C.x);
     ++H->launches;
-    for (int g = 0; g < H->o.cycle; ++g) cycle_rec(H, k - 1, C.f, C.x, s);
-    k_st_prolong<<<grid_of(D.m), 256, 0, s>>>(D.blocks(), C.blocks(), CsrDev{D.p2p, D.p2c, D.p2v},
-                                              CsrDev{D.p1p, D.p1c, D.p1v}, C.x, x);
+    if (k - 1 == H->kd) {
+        // the gamma coarse-grid iterations of levels <= kd from x = 0 are a
+        // fixed linear map of the restricted defect: x_c = B f_c
+        launch_pdl(k_st_dense, dim3(grid_of(C.m, 128), kDenseChunks), dim3(128), 0, s, C.m,
+                   (C.m + kDenseChunks - 1) / kDenseChunks, (const double*)H->B, (const double*)C.f, H->dpart);
+        launch_pdl(k_st_dense_sum, dim3(grid_of(C.m)), dim3(256), 0, s, C.m, (const double*)H->dpart, C.x);
+        H->launches += 2;
+    } else {
+        for (int g = 0; g < H->o.cycle; ++g) cycle_rec(H, k - 1, C.f, C.x, s);
+    }
+    launch_pdl(k_st_prolong, dim3(grid_of(D.m)), dim3(256), 0, s, D.blocks(), C.blocks(),
+               CsrDev{D.p2p, D.p2c, D.p2v}, CsrDev{D.p1p, D.p1c, D.p1v}, (const double*)C.x, x);
     ++H->launches;
     if (H->o.nu_post > 0) launch_smooth(H, k, f, x, H->o.nu_post, s);
+}
+
+// The dense map of levels <= kd: the gamma iterations of level kd from x = 0
+// applied to the unit vectors, a batch of them at a time (multi-vectors:
+// vector j at offset j m_k; one grid row per vector, or one block per vector
+// for whole smoothing calls on the small levels); the images are the map's
+// columns.
+struct Multi {
+    std::vector<double*> f, x, r, p;
+};
+
+void smooth_multi(ms_ctx* H, int k, Multi& W, int nc, int steps, cudaStream_t s) {
+    if (steps <= 0) return;
+    ms_ctx::Lev& D = H->lev[k];
+    const RowsDev S = D.rows();
+    const int sm = H->o.smoother;
+    const size_t smem = 3 * (size_t)D.m * sizeof(double);
+    if (smem <= 200 * 1024) {
+        launch_pdl(k_st_small, dim3(nc), dim3(kSmallThreads), smem, s, S, (const int*)D.poff_d, D.nph, sm, steps,
+                   H->o.tau, (const double*)W.f[k], W.x[k]);
+        return;
+    }
+    const int gr = grid_of((long long)D.nrows * kGroup);
+    launch_pdl(k_st_resid, dim3(gr, nc), dim3(256), 0, s, S, (const double*)W.f[k], (const double*)W.x[k], W.r[k]);
+    for (int m = 0; m < steps; ++m) {
+        if (sm == MS_SMOOTHER_NE) {
+            launch_pdl(k_st_ne_p, dim3(gr, nc), dim3(256), 0, s, S, H->o.tau, (const double*)W.r[k], W.p[k]);
+            launch_pdl(k_st_ne_update, dim3(gr, nc), dim3(256), 0, s, S, (const double*)W.p[k], W.x[k], W.r[k]);
+            continue;
+        }
+        for (int pass = 0; pass < (sm == MS_SMOOTHER_SLSGS ? 2 : 1); ++pass)
+            for (int q = 0; q < D.nph; ++q) {
+                const int ph = pass == 0 ? q : D.nph - 1 - q;
+                const int r0 = D.poff[ph], cnt = D.poff[ph + 1] - r0;
+                if (cnt > 0)
+                    launch_pdl(k_st_phase, dim3(grid_of((long long)cnt * kGroup), nc), dim3(256), 0, s, S, r0, cnt,
+                               W.x[k], W.r[k]);
+            }
+    }
+}
+
+void cycle_multi(ms_ctx* H, int k, Multi& W, int nc, cudaStream_t s) {
+    if (k == 1) {
+        launch_pdl(k_st_coarse, dim3(nc), dim3(256), 0, s, H->lev[1].m, (const double*)H->G, (const double*)W.f[1],
+                   W.x[1]);
+        return;
+    }
+    ms_ctx::Lev& D = H->lev[k];
+    ms_ctx::Lev& C = H->lev[k - 1];
+    smooth_multi(H, k, W, nc, H->o.nu_pre, s);
+    launch_pdl(k_st_resid, dim3(grid_of((long long)D.nrows * kGroup), nc), dim3(256), 0, s, D.rows(),
+               (const double*)W.f[k], (const double*)W.x[k], W.r[k]);
+    launch_pdl(k_st_restrict, dim3(grid_of(C.m), nc), dim3(256), 0, s, D.blocks(), C.blocks(),
+               CsrDev{D.r2p, D.r2c, D.r2v}, CsrDev{D.r1p, D.r1c, D.r1v}, (const double*)W.r[k], W.f[k - 1],
+               W.x[k - 1]);
+    for (int g = 0; g < H->o.cycle; ++g) cycle_multi(H, k - 1, W, nc, s);
+    launch_pdl(k_st_prolong, dim3(grid_of(D.m), nc), dim3(256), 0, s, D.blocks(), C.blocks(),
+               CsrDev{D.p2p, D.p2c, D.p2v}, CsrDev{D.p1p, D.p1c, D.p1v}, (const double*)W.x[k - 1], W.x[k]);
+    smooth_multi(H, k, W, nc, H->o.nu_post, s);
+}
+
+constexpr int kDenseBatch = 4096;  // unit vectors per pass of the dense map build
+
+int build_dense(ms_ctx* H) {
+    TraceRange tr("stokes: dense map of levels <= %d", H->kd);
+    const int kd = H->kd, m = H->lev[kd].m;
+    const int nb = std::min(m, kDenseBatch);
+    Multi W;
+    W.f.assign(kd + 1, nullptr);
+    W.x.assign(kd + 1, nullptr);
+    W.r.assign(kd + 1, nullptr);
+    W.p.assign(kd + 1, nullptr);
+    int rc = dev_upload<double>(H, H->B, nullptr, (size_t)m * m);
+    for (int k = 1; k <= kd && !rc; ++k) {
+        const size_t n = (size_t)H->lev[k].m * nb * sizeof(double);
+        if (cudaMalloc((void**)&W.f[k], n) != cudaSuccess || cudaMalloc((void**)&W.x[k], n) != cudaSuccess ||
+            cudaMalloc((void**)&W.r[k], n) != cudaSuccess || cudaMalloc((void**)&W.p[k], n) != cudaSuccess)
+            rc = set_error(AAOMG_ERR_OOM, "stokes dense map workspace");
+    }
+    cudaStream_t s = H->cap;
+    for (int j0 = 0; j0 < m && !rc; j0 += nb) {
+        const int nc = std::min(nb, m - j0);
+        const size_t n = (size_t)nc * m;
+        launch_pdl(k_st_identity, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, m, j0, nc, W.f[kd]);
+        cudaMemsetAsync(W.x[kd], 0, n * sizeof(double), s);
+        for (int g = 0; g < H->o.cycle; ++g) cycle_multi(H, kd, W, nc, s);
+        cudaMemcpyAsync(H->B + (size_t)j0 * m, W.x[kd], n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) rc = set_error(AAOMG_ERR_CUDA, std::string("stokes dense map: ") + cudaGetErrorString(e));
+    }
+    for (int k = 1; k <= kd; ++k) {
+        cudaFree(W.f[k]);
+        cudaFree(W.x[k]);
+        cudaFree(W.r[k]);
+        cudaFree(W.p[k]);
+    }
+    if (!rc) rc = dev_alloc(H, H->dpart, (size_t)kDenseChunks * m);
+    return rc;
 }
 
 int record_cycle(ms_ctx* H) {
@@ -968,14 +1196,14 @@ int record_cycle(ms_ctx* H) {
 void launch_norms(ms_ctx* H, int mode, const double* v, const double* g, const double* means, double* out,
                   cudaStream_t s) {
     ms_ctx::Lev& T = H->lev[H->L];
-    k_st_norm_part<<<kNormBlocks, 256, 0, s>>>(T.blocks(), mode, T.invL, v, g, means, H->part);
-    k_st_norm_final<<<1, 256, 0, s>>>(H->part, kNormBlocks, out);
+    launch_pdl(k_st_norm_part, dim3(kNormBlocks), dim3(256), 0, s, T.blocks(), mode, T.invL, v, g, means, H->part);
+    launch_pdl(k_st_norm_final, dim3(1), dim3(256), 0, s, H->part, kNormBlocks, out);
     H->launches += 2;
 }
 
 void launch_means(ms_ctx* H, const double* x, cudaStream_t s) {
     ms_ctx::Lev& T = H->lev[H->L];
-    k_st_means<<<1, 1024, 0, s>>>(T.blocks(), T.w, x, H->means);
+    launch_pdl(k_st_means, dim3(1), dim3(1024), 0, s, T.blocks(), T.w, x, H->means);
     ++H->launches;
 }
 
@@ -1025,6 +1253,8 @@ int ms_setup(int levels, double alpha, const ms_options* opt, ms_handle* out) {
     if (o.max_iter <= 0) o.max_iter = 100;
     if (o.block_max == 0) o.block_max = 4;
     if (o.block_max > 4) return set_error(AAOMG_ERR_BAD_ARG, "block_max must be at most 4");
+    if (o.dense_level > 5 || (o.dense_level > 0 && o.dense_level >= levels))
+        return set_error(AAOMG_ERR_BAD_ARG, "dense_level must be below levels and at most 5");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -1035,6 +1265,7 @@ int ms_setup(int levels, double alpha, const ms_options* opt, ms_handle* out) {
     H->L = levels;
     H->alpha = alpha;
     H->o = o;
+    H->kd = o.dense_level > 0 ? o.dense_level : (o.dense_level == 0 && levels >= 5 ? (levels >= 7 ? 5 : 4) : 0);
     cudaGetDevice(&H->device);
     H->lev.resize(levels + 1);
     int rc = AAOMG_OK;
@@ -1067,6 +1298,7 @@ int ms_setup(int levels, double alpha, const ms_options* opt, ms_handle* out) {
         rc = set_error(AAOMG_ERR_CUDA, "stokes small-level kernel attributes");
     if (!rc && cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking) != cudaSuccess)
         rc = set_error(AAOMG_ERR_CUDA, "stream creation");
+    if (!rc && H->kd > 0) rc = build_dense(H);
     if (!rc) rc = record_cycle(H);
     if (rc) {
         ms_destroy(H);
@@ -1104,7 +1336,7 @@ int ms_rhs_from_vd(ms_handle h, const double* vD, double* f, void* stream) {
     if (!vD || !f) return set_error(AAOMG_ERR_BAD_ARG, "null vector");
     auto& T = h->lev[h->L];
     const int ng = 2 * T.n + 1;
-    k_st_rhs<<<grid_of(T.m), 256, 0, (cudaStream_t)stream>>>(T.blocks(), ng * ng, CsrDev{h->mfp, h->mfc, h->mfv}, vD, f);
+    launch_pdl(k_st_rhs, dim3(grid_of(T.m)), dim3(256), 0, (cudaStream_t)stream, T.blocks(), ng * ng, CsrDev{h->mfp, h->mfc, h->mfv}, vD, f);
     ++h->launches;
     SCK(cudaGetLastError());
     return AAOMG_OK;
@@ -1197,7 +1429,7 @@ int ms_normalize(ms_handle h, double* x, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     auto& T = h->lev[h->L];
     launch_means(h, x, s);
-    k_st_shift<<<grid_of(T.np), 256, 0, s>>>(T.blocks(), h->means, x);
+    launch_pdl(k_st_shift, dim3(grid_of(T.np)), dim3(256), 0, s, T.blocks(), h->means, x);
     ++h->launches;
     SCK(cudaGetLastError());
     return AAOMG_OK;

@@ -33,6 +33,7 @@ class Options(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("max_iter", ctypes.c_int),
         ("block_max", ctypes.c_int),
+        ("dense_level", ctypes.c_int),
     ]
 
 
@@ -75,11 +76,12 @@ class StokesSolver:
     """One hierarchy (levels 1..L, h = 2^-L finest) for one alpha."""
 
     def __init__(self, levels: int, alpha: float, smoother: str = "lsgs", cycle: str = "W", nu_pre: int = 0,
-                 nu_post: int = 0, tau: float = 0.0, max_iter: int = 0, block_max: int = 0):
+                 nu_post: int = 0, tau: float = 0.0, max_iter: int = 0, block_max: int = 0,
+                 dense_level: int = 0):
         self._lib = load()
         self.levels, self.alpha, self.smoother = int(levels), float(alpha), smoother
         opt = Options(SMOOTHER[smoother], int(nu_pre), int(nu_post), CYCLE[cycle], float(tau), int(max_iter),
-                      int(block_max))
+                      int(block_max), int(dense_level))
         h = ctypes.c_void_p()
         _mg._check(self._lib.ms_setup(self.levels, self.alpha, ctypes.byref(opt), ctypes.byref(h)), "ms_setup")
         self._h = h

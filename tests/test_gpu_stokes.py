@@ -84,16 +84,22 @@ def test_smoothing_steps(st, stokes_mod, L, alpha, smoother, block_max):
             assert d <= 1e-11, (steps, d)
 
 
+@pytest.mark.parametrize("dense_level", [0, -1, 2])
 @pytest.mark.parametrize("cycle", ["W", "V"])
 @pytest.mark.parametrize("smoother", ["ne", "lsgs", "slsgs"])
-@pytest.mark.parametrize("L", [1, 2, 4, 6])
-def test_cycle(st, stokes_mod, L, smoother, cycle):
+@pytest.mark.parametrize("L", [1, 2, 4, 6, 7])
+def test_cycle(st, stokes_mod, L, smoother, cycle, dense_level):
+    """One cycle against the oracle's recursion down to h = 1/2, with the dense
+    map of the coarse levels (by default levels <= 4 at L = 6, levels <= 5 at
+    L = 7; or levels <= 2) and without it."""
+    if (dense_level > 0 and dense_level >= L) or (L == 7 and dense_level != 0):
+        pytest.skip("no coarser level to replace / one dense variant at L = 7")
     alpha = 1e-3
     nu = 1 if smoother == "slsgs" else 2
     o = stokes_mod.StokesOracle(L, alpha, smoother=smoother, nu_pre=nu, nu_post=nu, gamma=2 if cycle == "W" else 1)
     x0 = inputs.stokes_x_uniform(L, 30 + L)
     f = o.rhs(inputs.stokes_vd_vortex(L, 31))
-    with st.StokesSolver(L, alpha, smoother=smoother, cycle=cycle) as s:
+    with st.StokesSolver(L, alpha, smoother=smoother, cycle=cycle, dense_level=dense_level) as s:
         x = dev(x0)
         s.cycle(dev(f), x)
         xo = o.cycle(f, x0)
