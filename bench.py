@@ -98,6 +98,7 @@ def parse():
     p.add_argument("--no-l12", action="store_true", help="skip the h = 2^-12 single-instance line")
     p.add_argument("--no-batch256", action="store_true", help="skip the 256-instance batched-solve line")
     p.add_argument("--no-autograd", action="store_true", help="skip the 16-instance differentiation line")
+    p.add_argument("--no-stokes", action="store_true", help="skip the Stokes control line")
     p.add_argument("--profile-band", type=int, default=0, metavar="L",
                    help="for ncu captures: set up one FP32 LSGS handle at h = 2^-L and run --steps finest-level "
                         "smoothing steps (mg_smooth) after --warmup untimed ones; prints the CUDA-event time")
@@ -375,6 +376,8 @@ def run_ours(args, rank, world, local):
         out["batch256"] = batch_line(args, 256, steps=2, warmup=1)
     if not args.no_autograd and not args.profiling_run:
         out["autograd16"] = run_autograd16(args)
+    if not args.no_stokes and not args.profiling_run:
+        out["stokes"] = run_stokes(args, peak, pk is not None, flush, cpu=(rank == 0 and world == 1 and not args.no_cpu))
 
     if not args.no_fp64:
         sol64 = make("fp64", False)
@@ -881,6 +884,110 @@ def run_autograd16(args):
                          "dLdlogalpha_fd": fd_a, "rel_err_log_alpha": abs(gla - fd_a) / abs(fd_a)},
             "config": "16 x h=2^-10, alpha=1e-2, y_D ~ U(-1,1) seed 4, u_target ~ N(0,1) seed 3, LSGS W(2,2), "
                       "FP32+FP64-refine forward and adjoint solves to 1e-10, one batch graph each"}
+
+
+STOKES_GOLDEN = os.path.join(ROOT, "tests", "golden", "stokes_L{L}.json")
+
+
+def run_stokes(args, peak, measured, flush, cpu=True):
+    """The Stokes control problem (section 1, eq. (mp3); Taylor-Hood P2-P1):
+    h = 2^-9 (4,712,454 unknowns), alpha = 1e-4, desired velocity the
+    divergence-free vortex plus 0.1 N(0,1) noise (seed 1), LSGS W(2,2) in FP64
+    from x = 0 to a relative residual of 1e-8; one solve at a time, L2 flushed
+    before each.  The solution is checked at 256 sampled unknowns against the
+    oracle's (tests/golden/stokes_L9.json, solved to 1e-10).  Roofline of the
+    dominant kernel, the LSGS colour phases: one finest-level LSGS step (the
+    residual and 90 colour launches) timed with CUDA events over ten steps;
+    algorithmic bytes per step: the matrix once (column, A_ij, A_ij / L_jj:
+    20 B per nonzero), the row data (index, length, start, 1 / N_ii: 24 B per
+    unknown), x and r read and written once (32 B per unknown), and the
+    residual's pass (12 B per nonzero, f read and r written: 16 B per
+    unknown).  CPU baseline: a complete oracle solve of the same workload at
+    h = 2^-7 (293,382 unknowns), timed on this host."""
+    import numpy as np
+    import torch
+
+    from paper_1502_03917_gb300 import inputs
+    from paper_1502_03917_gb300 import stokes
+
+    L, a, tol = 9, 1e-4, 1e-8
+    vD = torch.tensor(inputs.stokes_vd_vortex(L, 1), dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    s = stokes.StokesSolver(L, a, smoother="lsgs", max_iter=100)
+    setup_s = time.time() - t0
+    f = s.rhs_from_vd(vD)
+    x = torch.zeros_like(f)
+    s.solve(f, x, tol=tol)
+    K = 3
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    it = rr = None
+    launches0 = s.kernel_launches()
+    for k in range(K):
+        flush.fill_(float(k))
+        x.zero_()
+        ev[k][0].record()
+        it, rr, _ = s.solve(f, x, tol=tol)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    launches = (s.kernel_launches() - launches0) // K
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / K
+    err = None
+    gpath = STOKES_GOLDEN.format(L=L)
+    if os.path.exists(gpath):
+        g = json.load(open(gpath))
+        ref = next(r for r in g["runs"] if r["alpha"] == a)
+        idx = np.array(g["sample"])
+        s.normalize(x)
+        xs = x.cpu().numpy()[idx]
+        xo = np.array(ref["x"])
+        nv, npn, _ = inputs.stokes_sizes(L)
+        blk = np.searchsorted(np.array([nv, 2 * nv, 2 * nv + npn, 3 * nv + npn, 4 * nv + npn]), idx, side="right")
+        err = max(float(np.abs(xs[blk == b] - xo[blk == b]).max() / np.abs(xo[blk == b]).max())
+                  for b in np.unique(blk))
+    # the finest-level LSGS step
+    nnz, stored = s.operator_entries()
+    steps = 10
+    s.smooth(f, x, 2)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.smooth(f, x, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / steps
+    m = s.m
+    phase_bytes = 20 * nnz + (24 + 32) * m
+    resid_bytes = 12 * nnz + 16 * m
+    achieved = (phase_bytes + resid_bytes / steps) / (step_ms / 1e3) / 1e9
+    s.close()
+    out = {"metric": "solved unknowns/s at 1e-8 rel. residual (FP64)", "value": m / (ms / 1e3),
+           "unit": "unknowns/s", "ms_per_solve": ms, "solves_timed": K, "iterations": it, "relres": rr,
+           "setup_s": setup_s, "gpu_launches_per_solve": launches, "error_vs_oracle": err,
+           "config": {"workload": f"Stokes control (Taylor-Hood P2-P1), h=2^-{L} ({m} unknowns), alpha={a:g}, "
+                                  f"v_D = vortex + 0.1 N(0,1) seed 1, LSGS W(2,2) to h=1/2 (levels <= 5 as one "
+                                  f"dense map), FP64, tol {tol}", "l2": "flushed (256 MB write) before every solve"},
+           "roofline": {"bound": "hbm", "kernel": "finest-level LSGS step (residual + 90 colour phases, k_st_phase)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": "measured" if measured else "fallback", "traffic": None,
+                        "step_ms": step_ms, "nnz": nnz, "entries_held": stored,
+                        "algorithmic_bytes_per_step": phase_bytes + resid_bytes}}
+    if cpu:
+        from oracle.stokes import StokesOracle
+
+        Lc = 7
+        o = StokesOracle(Lc, a, smoother="lsgs")
+        fo = o.rhs(inputs.stokes_vd_vortex(Lc, 1))
+        t1 = time.time()
+        _, ito, _, _ = o.solve(fo, tol=tol, max_iter=100)
+        sec = time.time() - t1
+        mo = o.m()
+        o.close()
+        out["cpu_baseline"] = {"value": mo / sec, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                               "sample": f"one complete oracle solve of the same workload at h=2^-{Lc} ({mo} "
+                                         f"unknowns, {ito} cycles, {sec:.1f} s), set-up excluded",
+                               "host": host_cpu()}
+    return out
 
 
 def main():

@@ -135,6 +135,12 @@ AAOMG_API int ms_protocol_iterations(ms_handle h, const double* x0, double reduc
 /* Number of kernels the library launched for this handle since ms_setup. */
 AAOMG_API long long ms_kernel_launches(ms_handle h);
 
+/* Entries of A on level `level`: *nnz the nonzeros of eq. (mp3)'s matrix as
+ * assembled, *stored the entries the library holds (each row padded to a
+ * multiple of 8).  For the algorithmic bytes of a smoothing step.  Errors:
+ * BAD_ARG. */
+AAOMG_API int ms_operator_entries(ms_handle h, int level, long long* nnz, long long* stored);
+
 #ifdef __cplusplus
 }
 #endif

@@ -848,6 +848,7 @@ struct ms_ctx {
         double *p2v = nullptr, *p1v = nullptr, *r2v = nullptr, *r1v = nullptr;
         double *x = nullptr, *f = nullptr, *r = nullptr, *p = nullptr;
         bool small = false;
+        long long nnz = 0, stored = 0;  // entries of A; entries held (rows padded to multiples of kGroup)
         RowsDev rows() const {
             return RowsDev{m, nrows, rowid, len, start, col, a, al, invN, invL};
         }
@@ -952,6 +953,9 @@ int build_level(ms_ctx* H, const HostLevel& HL, ms_ctx::Lev& D) {
         start[row + 1] = start[row] + len[row];
     }
     const size_t ne = (size_t)start[D.nrows];
+    D.stored = (long long)ne;
+    D.nnz = 0;
+    for (int u = 0; u < HL.m; ++u) D.nnz += rowlen[u];
     std::vector<int> col(ne, 0);
     std::vector<double> a(ne, 0.0), al(ne, 0.0), invN(D.nrows, 0.0);
     for (int row = 0; row < D.nrows; ++row) {
@@ -1480,5 +1484,13 @@ int ms_protocol_iterations(ms_handle h, const double* x0, double reduction, int 
 }
 
 long long ms_kernel_launches(ms_handle h) { return h ? h->launches : -1; }
+
+int ms_operator_entries(ms_handle h, int level, long long* nnz, long long* stored) {
+    if (!h || !nnz || !stored) return set_error(AAOMG_ERR_BAD_ARG, "null argument");
+    if (level < 1 || level > h->L) return set_error(AAOMG_ERR_BAD_ARG, "level out of range");
+    *nnz = h->lev[level].nnz;
+    *stored = h->lev[level].stored;
+    return AAOMG_OK;
+}
 
 }  // extern "C"

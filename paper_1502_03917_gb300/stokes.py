@@ -63,6 +63,7 @@ def load():
             "ms_norms": (I, [H, P, pD, pD, P]),
             "ms_protocol_iterations": (I, [H, P, D, I, pI, P]),
             "ms_kernel_launches": (ctypes.c_longlong, [H]),
+            "ms_operator_entries": (I, [H, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -159,3 +160,10 @@ class StokesSolver:
 
     def kernel_launches(self) -> int:
         return int(self._lib.ms_kernel_launches(self._h))
+
+    def operator_entries(self, level: int | None = None):
+        """(nonzeros of A, entries held) on a level (the finest by default)."""
+        nnz, stored = ctypes.c_longlong(), ctypes.c_longlong()
+        _mg._check(self._lib.ms_operator_entries(self._h, self.levels if level is None else int(level),
+                                                 ctypes.byref(nnz), ctypes.byref(stored)), "ms_operator_entries")
+        return nnz.value, stored.value
