@@ -99,6 +99,12 @@ def parse():
     p.add_argument("--no-batch256", action="store_true", help="skip the 256-instance batched-solve line")
     p.add_argument("--no-autograd", action="store_true", help="skip the 16-instance differentiation line")
     p.add_argument("--no-stokes", action="store_true", help="skip the Stokes control line")
+    p.add_argument("--profile-stokes", type=int, default=0, metavar="L",
+                   help="profiling run: one Stokes W-cycle at h = 2^-L (bench workload, after a warm-up cycle) "
+                        "inside cudaProfilerStart/Stop (ncu --profile-from-start off)")
+    p.add_argument("--profile-stokes-step", type=int, default=0, metavar="L",
+                   help="profiling run: one finest-level Stokes LSGS step at h = 2^-L without the dense map "
+                        "inside cudaProfilerStart/Stop")
     p.add_argument("--profile-band", type=int, default=0, metavar="L",
                    help="for ncu captures: set up one FP32 LSGS handle at h = 2^-L and run --steps finest-level "
                         "smoothing steps (mg_smooth) after --warmup untimed ones; prints the CUDA-event time")
@@ -990,10 +996,43 @@ def run_stokes(args, peak, measured, flush, cpu=True):
     return out
 
 
+def run_profile_stokes(args):
+    """Profiling runs of the Stokes path (bench workload: alpha = 1e-4, LSGS,
+    the vortex desired velocity of seed 1): one W-cycle, or one finest-level
+    LSGS step of a hierarchy without the dense map (a small device footprint),
+    between cudaProfilerStart and cudaProfilerStop."""
+    import torch
+
+    from paper_1502_03917_gb300 import inputs
+    from paper_1502_03917_gb300 import stokes
+
+    L = args.profile_stokes or args.profile_stokes_step
+    step = not args.profile_stokes
+    s = stokes.StokesSolver(L, 1e-4, smoother="lsgs", dense_level=-1 if step else 0)
+    f = s.rhs_from_vd(torch.tensor(inputs.stokes_vd_vortex(L, 1), dtype=torch.float64, device="cuda"))
+    x = torch.zeros_like(f)
+    if not step:
+        s.cycle(f, x)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    if step:
+        s.smooth(f, x, 1)
+    else:
+        s.cycle(f, x)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile": "stokes step" if step else "stokes cycle", "level": L, "unknowns": s.m,
+                      "launches": s.kernel_launches()}))
+    s.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.profile_band:
+    if args.profile_stokes or args.profile_stokes_step:
+        if rank == 0:
+            run_profile_stokes(args)
+    elif args.profile_band:
         if rank == 0:
             run_profile_band(args)
     elif args.batch:
