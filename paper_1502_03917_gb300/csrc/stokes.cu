@@ -79,27 +79,44 @@ struct RowsDev {
     const double* invL;      // 1 / L_ii, natural order
 };
 
+// A row's data, loaded together (none of these loads waits for another):
+// natural index (-1: padding or no row), padded length, first entry, 1 / N_ii.
+struct RowHead {
+    int i, n;
+    long long b;
+    double invN;
+};
+
+__device__ __forceinline__ RowHead row_head(const RowsDev& S, int row) {
+    RowHead h{-1, 0, 0, 0.0};
+    if (row >= 0 && row < S.nrows) {
+        h.i = S.rowid[row];
+        h.n = S.len[row];
+        h.b = S.start[row];
+        h.invN = S.invN[row];
+    }
+    if (h.i < 0) h.n = 0;
+    return h;
+}
+
 // The kGroup lanes of a group (aligned within a warp) share one row: lane l
 // takes the entries l, l + kGroup, ...; all its loads are issued before their
 // first use, the partial sums meet by shuffles.  Every lane of the group gets
-// the row's sum; row < 0: zero (every lane of the warp still takes part in the
-// shuffles).
-__device__ __forceinline__ double group_dot(const RowsDev& S, int row, int lane, const double* v, const double* w) {
+// the row's sum; an empty row (n = 0) gives zero (every lane of the warp still
+// takes part in the shuffles).
+__device__ __forceinline__ double group_dot(const RowsDev& S, const RowHead& h, int lane, const double* v,
+                                           const double* w) {
     double acc = 0.0;
-    if (row >= 0) {
-        const int n = S.len[row];
-        const long long b = S.start[row] + lane;
-        int c[kMaxPerLane];
-        double wk[kMaxPerLane];
+    int c[kMaxPerLane];
+    double wk[kMaxPerLane];
 #pragma unroll
-        for (int u = 0; u < kMaxPerLane; ++u) {
-            const bool on = lane + u * kGroup < n;
-            c[u] = on ? S.col[b + u * kGroup] : 0;
-            wk[u] = on ? w[b + u * kGroup] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kMaxPerLane; ++u) acc += wk[u] * v[c[u]];
+    for (int u = 0; u < kMaxPerLane; ++u) {
+        const bool on = lane + u * kGroup < h.n;
+        c[u] = on ? S.col[h.b + lane + u * kGroup] : 0;
+        wk[u] = on ? w[h.b + lane + u * kGroup] : 0.0;
     }
+#pragma unroll
+    for (int u = 0; u < kMaxPerLane; ++u) acc += wk[u] * v[c[u]];
 #pragma unroll
     for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kGroup);
     return acc;
@@ -109,33 +126,30 @@ __device__ __forceinline__ double group_dot(const RowsDev& S, int row, int lane,
 // gather q = sum_j A_ij r_j / L_jj, p = q / N_ii, x_i += p, scatter
 // r_j -= A_ji p (A symmetric: the row's own entries).  No other row of the
 // colour touches these r_j, so the scatter reuses the gathered values and
-// indices: every load of the row is issued at the start.  row < 0 or a
-// padding row: shuffles only.
+// indices: a row costs three dependent memory round trips (its head, its
+// entries, the residual entries they address).  row < 0 or a padding row:
+// shuffles only.
 __device__ __forceinline__ void group_lsgs(const RowsDev& S, int row, int lane, double* x, double* r) {
-    const int i = row >= 0 ? S.rowid[row] : -1;
+    const RowHead h = row_head(S, row);
     int c[kMaxPerLane];
     double wl[kMaxPerLane], ak[kMaxPerLane], rk[kMaxPerLane];
-    double acc = 0.0;
-    if (i >= 0) {
-        const int n = S.len[row];
-        const long long b = S.start[row] + lane;
 #pragma unroll
-        for (int u = 0; u < kMaxPerLane; ++u) {
-            const bool on = lane + u * kGroup < n;
-            c[u] = on ? S.col[b + u * kGroup] : -1;
-            wl[u] = on ? S.al[b + u * kGroup] : 0.0;
-            ak[u] = on ? S.a[b + u * kGroup] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kMaxPerLane; ++u) rk[u] = c[u] >= 0 ? r[c[u]] : 0.0;
-#pragma unroll
-        for (int u = 0; u < kMaxPerLane; ++u) acc += wl[u] * rk[u];
+    for (int u = 0; u < kMaxPerLane; ++u) {
+        const bool on = lane + u * kGroup < h.n;
+        c[u] = on ? S.col[h.b + lane + u * kGroup] : -1;
+        wl[u] = on ? S.al[h.b + lane + u * kGroup] : 0.0;
+        ak[u] = on ? S.a[h.b + lane + u * kGroup] : 0.0;
     }
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < kMaxPerLane; ++u) rk[u] = c[u] >= 0 ? r[c[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kMaxPerLane; ++u) acc += wl[u] * rk[u];
 #pragma unroll
     for (int o = kGroup / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kGroup);
-    if (i < 0) return;
-    const double p = acc * S.invN[row];
-    if (lane == 0) x[i] += p;
+    if (h.i < 0) return;
+    const double p = acc * h.invN;
+    if (lane == 0) x[h.i] += p;
 #pragma unroll
     for (int u = 0; u < kMaxPerLane; ++u)
         if (c[u] >= 0 && ak[u] != 0.0) r[c[u]] = rk[u] - ak[u] * p;
@@ -161,8 +175,9 @@ __global__ void k_st_resid(RowsDev S, const double* f, const double* x, double* 
     r += vo;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = t / kGroup, lane = t % kGroup;
-    const int i = row < S.nrows ? S.rowid[row] : -1;
-    const double s = group_dot(S, i >= 0 ? row : -1, lane, x, S.a);
+    const RowHead h = row_head(S, row);
+    const int i = h.i;
+    const double s = group_dot(S, h, lane, x, S.a);
     if (i >= 0 && lane == 0) r[i] = f[i] - s;
 }
 
@@ -174,8 +189,9 @@ __global__ void k_st_ne_p(RowsDev S, double tau, const double* r, double* p) {
     p += vo;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = t / kGroup, lane = t % kGroup;
-    const int i = row < S.nrows ? S.rowid[row] : -1;
-    const double q = group_dot(S, i >= 0 ? row : -1, lane, r, S.al);
+    const RowHead h = row_head(S, row);
+    const int i = h.i;
+    const double q = group_dot(S, h, lane, r, S.al);
     if (i >= 0 && lane == 0) p[i] = tau * q * S.invL[i];
 }
 
@@ -189,8 +205,9 @@ __global__ void k_st_ne_update(RowsDev S, const double* p, double* x, double* r)
     r += vo;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = t / kGroup, lane = t % kGroup;
-    const int i = row < S.nrows ? S.rowid[row] : -1;
-    const double s = group_dot(S, i >= 0 ? row : -1, lane, p, S.a);
+    const RowHead h = row_head(S, row);
+    const int i = h.i;
+    const double s = group_dot(S, h, lane, p, S.a);
     if (i >= 0 && lane == 0) {
         x[i] += p[i];
         r[i] -= s;
@@ -217,22 +234,25 @@ __global__ void __launch_bounds__(kSmallThreads)
     for (int i = g; i < S.m; i += G) xs[i] = x[i];
     __syncthreads();
     for (int row = grp; row < nrow_pad; row += NG) {
-        const int i = row < S.nrows ? S.rowid[row] : -1;
-        const double s = group_dot(S, i >= 0 ? row : -1, lane, xs, S.a);
+        const RowHead h = row_head(S, row);
+        const int i = h.i;
+        const double s = group_dot(S, h, lane, xs, S.a);
         if (i >= 0 && lane == 0) rs[i] = f[i] - s;
     }
     __syncthreads();
     for (int m = 0; m < steps; ++m) {
         if (smoother == 0) {
             for (int row = grp; row < nrow_pad; row += NG) {
-                const int i = row < S.nrows ? S.rowid[row] : -1;
-                const double q = group_dot(S, i >= 0 ? row : -1, lane, rs, S.al);
+                const RowHead h = row_head(S, row);
+                const int i = h.i;
+                const double q = group_dot(S, h, lane, rs, S.al);
                 if (i >= 0 && lane == 0) ps[i] = tau * q * S.invL[i];
             }
             __syncthreads();
             for (int row = grp; row < nrow_pad; row += NG) {
-                const int i = row < S.nrows ? S.rowid[row] : -1;
-                const double s = group_dot(S, i >= 0 ? row : -1, lane, ps, S.a);
+                const RowHead h = row_head(S, row);
+                const int i = h.i;
+                const double s = group_dot(S, h, lane, ps, S.a);
                 if (i >= 0 && lane == 0) {
                     xs[i] += ps[i];
                     rs[i] -= s;
