@@ -99,6 +99,8 @@ def parse():
     p.add_argument("--no-batch256", action="store_true", help="skip the 256-instance batched-solve line")
     p.add_argument("--no-autograd", action="store_true", help="skip the 16-instance differentiation line")
     p.add_argument("--no-stokes", action="store_true", help="skip the Stokes control line")
+    p.add_argument("--protocol-stokes", action="store_true",
+                   help="the section 3 protocol for the Stokes control problem on the GPU, in the layout of Table 2")
     p.add_argument("--profile-stokes", type=int, default=0, metavar="L",
                    help="profiling run: one Stokes W-cycle at h = 2^-L (bench workload, after a warm-up cycle) "
                         "inside cudaProfilerStart/Stop (ncu --profile-from-start off)")
@@ -751,6 +753,42 @@ def run_protocol(args):
                       "seconds": time.time() - t0, "rows": rows}))
 
 
+def run_protocol_stokes(args):
+    """Section 3's protocol for the Stokes control problem on the GPU, laid out
+    like Table 2: zero right-hand side, random start U(-1,1) (seed 7),
+    W-cycles with 2+2 steps (sLSGS 1+1, NE damped with tau = 0.35) until the
+    error in the L norm (means of p and mu removed) has dropped by 1e-6, for
+    k = 4..7 and alpha in {1, 1e-6, 1e-12}, beside the paper's counts (natural
+    order of Algorithm 2; the GPU visits the unknowns in the multicolour
+    order)."""
+    import numpy as np
+    import torch
+
+    from paper_1502_03917_gb300 import build as B
+    from paper_1502_03917_gb300 import inputs
+    from paper_1502_03917_gb300 import stokes
+
+    B.build()
+    paper = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table2_iterations.txt")) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) == 4 and not line.startswith("#"):
+                paper[(parts[0], int(parts[1]), float(parts[2]))] = int(parts[3])
+    rows = []
+    t0 = time.time()
+    for sm in ("ne", "lsgs", "slsgs"):
+        for k in (4, 5, 6, 7):
+            x0 = torch.tensor(np.random.default_rng(7).uniform(-1.0, 1.0, inputs.stokes_sizes(k)[2]),
+                              dtype=torch.float64, device="cuda")
+            for a in (1.0, 1e-6, 1e-12):
+                with stokes.StokesSolver(k, a, smoother=sm) as s:
+                    rows.append({"smoother": sm, "k": k, "alpha": a, "paper": paper.get((sm, k, a)),
+                                 "gpu_fp64": s.protocol_iterations(x0, 1e-6, 300)})
+    print(json.dumps({"protocol": "section 3 (Table 2 layout), Stokes control, Taylor-Hood, W-cycle, coarsest "
+                                  "h = 1/2, multicolour order", "seconds": time.time() - t0, "rows": rows}))
+
+
 def batch_line(args, count, steps, warmup):
     """The batched-solve configuration: `count` independent instances with
     levels uniform in 6..10, alpha log-uniform in [1e-8, 1], y_D ~ U(-1, 1)
@@ -1041,6 +1079,9 @@ def main():
     elif args.protocol:
         if rank == 0:
             run_protocol(args)
+    elif args.protocol_stokes:
+        if rank == 0:
+            run_protocol_stokes(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -120,6 +120,11 @@ AAOMG_API int ms_solve(ms_handle h, const double* f, double* x, double tol, int*
  * Errors: BAD_ARG, CUDA. */
 AAOMG_API int ms_normalize(ms_handle h, double* x, void* stream);
 
+/* The control u = lambda / alpha (section 1: it is recovered from the Lagrange
+ * multiplier) from a solution x: u has 2 nv doubles, first component then
+ * second, on the interior P2 nodes.  x, u: device.  Errors: BAD_ARG, CUDA. */
+AAOMG_API int ms_control(ms_handle h, const double* x, double* u, void* stream);
+
 /* ||x||_L and ||x||_{L^-1} on the finest level (either pointer may be NULL;
  * synchronises).  Errors: BAD_ARG, CUDA. */
 AAOMG_API int ms_norms(ms_handle h, const double* x, double* norm_L, double* norm_Linv, void* stream);

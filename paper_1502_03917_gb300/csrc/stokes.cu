@@ -434,6 +434,13 @@ __global__ void k_st_means(Blocks B, const double* __restrict__ w, const double*
     }
 }
 
+// u = lambda / alpha: the control (both components) from the adjoint velocity
+__global__ void k_st_control(Blocks B, double inv_alpha, const double* __restrict__ x, double* __restrict__ u) {
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 2 * B.nv) u[t] = x[B.off(3) + t] * inv_alpha;
+}
+
 __global__ void k_st_shift(Blocks B, const double* __restrict__ means, double* __restrict__ x) {
     pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1454,6 +1461,18 @@ int ms_normalize(ms_handle h, double* x, void* stream) {
     auto& T = h->lev[h->L];
     launch_means(h, x, s);
     launch_pdl(k_st_shift, dim3(grid_of(T.np)), dim3(256), 0, s, T.blocks(), h->means, x);
+    ++h->launches;
+    SCK(cudaGetLastError());
+    return AAOMG_OK;
+}
+
+int ms_control(ms_handle h, const double* x, double* u, void* stream) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x || !u) return set_error(AAOMG_ERR_BAD_ARG, "null vector");
+    auto& T = h->lev[h->L];
+    launch_pdl(k_st_control, dim3(grid_of(2LL * T.nv)), dim3(256), 0, (cudaStream_t)stream, T.blocks(),
+               1.0 / h->alpha, x, u);
     ++h->launches;
     SCK(cudaGetLastError());
     return AAOMG_OK;

@@ -60,6 +60,7 @@ def load():
             "ms_cycle": (I, [H, P, P, P]),
             "ms_solve": (I, [H, P, P, D, pI, pD, P]),
             "ms_normalize": (I, [H, P, P]),
+            "ms_control": (I, [H, P, P, P]),
             "ms_norms": (I, [H, P, pD, pD, P]),
             "ms_protocol_iterations": (I, [H, P, D, I, pI, P]),
             "ms_kernel_launches": (ctypes.c_longlong, [H]),
@@ -145,6 +146,15 @@ class StokesSolver:
 
     def normalize(self, x):
         _mg._check(self._lib.ms_normalize(self._h, _mg._dptr(x, self.m), _mg._stream()), "ms_normalize")
+
+    def control(self, x, u=None):
+        """u = lambda / alpha (both components on the interior P2 nodes)."""
+        import torch
+
+        u = torch.empty(2 * self.nv, dtype=torch.float64, device=x.device) if u is None else u
+        _mg._check(self._lib.ms_control(self._h, _mg._dptr(x, self.m), _mg._dptr(u, 2 * self.nv), _mg._stream()),
+                   "ms_control")
+        return u
 
     def norms(self, x):
         nl, ni = ctypes.c_double(), ctypes.c_double()

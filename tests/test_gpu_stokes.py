@@ -161,6 +161,16 @@ def test_normalize_and_norms(st, stokes_mod):
         assert d <= 1e-14
 
 
+def test_control_is_lambda_over_alpha(st):
+    L, alpha = 3, 1e-3
+    nv, npn, m = inputs.stokes_sizes(L)
+    x0 = inputs.stokes_x_uniform(L, 60)
+    with st.StokesSolver(L, alpha) as s:
+        u = host(s.control(dev(x0)))
+    lam = x0[2 * nv + npn: 4 * nv + npn]
+    np.testing.assert_array_equal(u, lam * (1.0 / alpha))
+
+
 def test_errors_and_launch_count(st):
     with st.StokesSolver(3, 1.0) as s:
         f = torch.zeros(s.m, dtype=torch.float64, device="cuda")
