@@ -171,6 +171,28 @@ def test_control_is_lambda_over_alpha(st):
     np.testing.assert_array_equal(u, lam * (1.0 / alpha))
 
 
+def test_not_converged_and_bad_arguments(st):
+    """A solve capped below the cycles it needs returns NOT_CONVERGED with the
+    iterate of its last cycle; invalid arguments are rejected before any
+    device work."""
+    from paper_1502_03917_gb300 import aaomg as mg
+
+    L = 4
+    with st.StokesSolver(L, 1e-2, max_iter=2) as s:
+        f = s.rhs_from_vd(dev(inputs.stokes_vd_vortex(L, 1)))
+        x = torch.zeros_like(f)
+        it, rr, code = s.solve(f, x, tol=1e-12, raise_on_fail=False)
+        assert code == mg.ERR_NOT_CONVERGED and it == 2 and 0 < rr < 1
+        with pytest.raises(mg.MGError):
+            s.solve(f, x, tol=1e-12)
+        with pytest.raises(mg.MGError):
+            s.sizes(L + 1)
+    with pytest.raises(mg.MGError):
+        st.StokesSolver(3, 1.0, dense_level=3)
+    with pytest.raises(mg.MGError):
+        st.StokesSolver(10, 1.0)
+
+
 def test_errors_and_launch_count(st):
     with st.StokesSolver(3, 1.0) as s:
         f = torch.zeros(s.m, dtype=torch.float64, device="cuda")
