@@ -328,8 +328,15 @@ def run_ours(args, rank, world, local):
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
     roofline = None
+    roofs = None
     if not args.profiling_run:
         roofline = sweep_roofline(mg, L, yD, 1e-4, args, peak, pk is not None)
+        # the project's own measurements of the roofs (FMA rates, L2-resident
+        # and HBM bandwidth): at 2049^2 the sweep's x and f (67 MB) fit in L2
+        roofs = mg.device_peaks()
+        if roofline and roofline.get("achieved"):
+            roofline["l2_gbs"] = roofs["l2_gbs"]
+            roofline["frac_of_l2"] = roofline["achieved"] / roofs["l2_gbs"]
         # share of the timed steps: the isolated sweep time times the finest
         # sweeps the timed solves ran (refinement steps x inner cycles x 4)
         per_iter = roofline.pop("sweeps_per_iteration")
@@ -374,7 +381,8 @@ def run_ours(args, rank, world, local):
                       "concurrency": 1 if args.serial else len(ALPHAS),
                       "kernels": "autotuned at set-up" if args.autotune else "measured defaults"},
            "iterations": {str(a): its32[a] for a in ALPHAS},
-           "roofline": roofline, "roofline_by_time": by_time, "clocks": clocks, "gpu_launches": launches}
+           "roofline": roofline, "roofline_by_time": by_time, "roofs_measured": roofs, "clocks": clocks,
+           "gpu_launches": launches}
 
     out["error_vs_oracle"] = error_vs_golden(L, {a: xs32[a] for a in ALPHAS}, args.smoother)
 
@@ -400,6 +408,8 @@ def run_ours(args, rank, world, local):
         out["fp64_plain"] = {"value": world * unknowns_step * K64 / (ms64 / 1e3), "ms_per_step": ms64 / K64,
                              "iterations": {str(a): its64[a] for a in ALPHAS},
                              "max_rel_diff_fp32refine_vs_fp64": err}
+        if roofs and args.smoother == "lsgs" and not args.profiling_run:
+            out["fp64_plain"]["roofline"] = sweep_roofline_fp64(mg, L, yD, args, roofs)
         for s in sol64.values():
             s.close()
 
@@ -455,6 +465,36 @@ def sweep_roofline(mg, L, yD, alpha, args, peak, measured):
             "timing": f"one solve alone (alpha={alpha:g}), CUDA events in the solver graph around each "
                       "finest-level smoothing call",
             "sweeps_per_iteration": nsw / it if it else 0}
+
+
+FLOPS_LSGS_NODE = 114  # Algorithm 2 per node and step: two unknowns, each 14 gather + 14 scatter FMAs and p
+
+
+def sweep_roofline_fp64(mg, L, yD, args, roofs):
+    """The FP64 path's finest-level LSGS sweep (per-colour launches), timed as
+    `sweep_roofline` does, against the FP64 FMA rate measured by
+    mg_device_peaks: algorithmic flops per node and step = Algorithm 2's, two
+    unknowns each with 14 gather and 14 scatter FMAs (A has 14 entries per
+    node row over both fields) and one multiply: 114."""
+    s = mg.Solver(L, 1e-4, smoother="lsgs", precision="fp64", cycle=args.cycle, max_iter=100, profile=True)
+    f = s.rhs_from_yd(yD)
+    import torch
+
+    x = torch.zeros_like(f)
+    s.solve(f, x, tol=args.tol)
+    s.reset_profile()
+    x.zero_()
+    s.solve(f, x, tol=args.tol)
+    t_ms, nsw = s.profile()
+    s.close()
+    N = ((1 << L) + 1) ** 2
+    sweep_ms = t_ms / nsw if nsw else None
+    tflops = FLOPS_LSGS_NODE * N / (sweep_ms * 1e-3) / 1e12 if sweep_ms else None
+    return {"bound": "fp64", "kernel": f"finest-level FP64 LSGS sweep (per-colour launches, h=2^-{L})",
+            "achieved": tflops, "peak": roofs["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": tflops / roofs["fp64_tflops"] if tflops else None, "peak_source": "mg_device_peaks",
+            "sweep_ms": sweep_ms, "sweeps_timed": nsw, "algorithmic_flops_per_sweep": FLOPS_LSGS_NODE * N,
+            "hbm_gbs": 48 * N / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None}
 
 
 def error_vs_golden(L, xs, smoother):

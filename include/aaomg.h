@@ -304,6 +304,15 @@ AAOMG_API int mg_residual_noalloc(int levels, double alpha, int k_variant, const
                                   double* relres, void* stream);
 
 /* Name of an AAOMG_* code; message of the calling thread's last failure. */
+/* The roofs of the library's kernels on the current device, measured with the
+ * library's own microbenchmarks (the paper has no counterpart: measurement
+ * only): the FP32 fused multiply-add rate (packed pairs, as the FP32 kernels
+ * compute), the FP64 fused multiply-add rate, the read bandwidth of data
+ * resident in L2 (a buffer of a quarter of the L2 size read repeatedly) and the
+ * HBM copy bandwidth (2 GB read and 2 GB written).  Allocates about 4 GB for
+ * the call and synchronises the device.  Errors: BAD_ARG, NO_DEVICE, OOM, CUDA. */
+AAOMG_API int mg_device_peaks(double* fp32_tflops, double* fp64_tflops, double* l2_gbs, double* hbm_gbs);
+
 AAOMG_API const char* mg_strerror(int code);
 AAOMG_API const char* mg_last_error(void);
 

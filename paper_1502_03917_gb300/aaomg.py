@@ -102,6 +102,7 @@ def load():
                                      pD, D, pI, P]),
             "mg_control": (I, [H, P, P, P]),
             "mg_adjoint": (I, [H, P, P, P, P, pD, D, P]),
+            "mg_device_peaks": (I, [pD, pD, pD, pD]),
             "mg_strerror": (ctypes.c_char_p, [I]),
             "mg_last_error": (ctypes.c_char_p, []),
         }
@@ -134,6 +135,15 @@ def _dptr(t, n=None):
     if n is not None and t.numel() != n:
         raise ValueError(f"expected {n} elements, got {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def device_peaks() -> dict:
+    """The current device's FP32 and FP64 FMA rates (TFLOP/s), L2-resident read
+    bandwidth and HBM copy bandwidth (GB/s), measured by mg_device_peaks."""
+    lib = load()
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib.mg_device_peaks(*[ctypes.byref(x) for x in v]), "mg_device_peaks")
+    return {"fp32_tflops": v[0].value, "fp64_tflops": v[1].value, "l2_gbs": v[2].value, "hbm_copy_gbs": v[3].value}
 
 
 def residual_noalloc(levels: int, alpha: float, f, x, r=None, k_variant: int = 0):

@@ -469,3 +469,12 @@ def test_constant_desired_state(mg):
         xh = host(x)
         np.testing.assert_allclose(xh[: s.N], c / (1 + alpha), rtol=1e-9)
         np.testing.assert_allclose(xh[s.N:], alpha * c / (1 + alpha), rtol=1e-8)
+
+
+def test_device_peaks_are_plausible(mg):
+    """The microbenchmarks behind the roofline report rates in the order the
+    hardware has them: packed FP32 far above FP64, L2-resident reads above the
+    HBM copy, and an HBM copy bandwidth of a few TB/s."""
+    p = mg.device_peaks()
+    assert p["fp32_tflops"] > 10 * p["fp64_tflops"] > 0
+    assert p["l2_gbs"] > p["hbm_copy_gbs"] > 1000
