@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""Benchmark of the all-at-once multigrid solver for the Poisson control problem.
+"""Benchmark of the all-at-once multigrid solvers for the Poisson and Stokes control problems.
 
 Workload (one "step"): the scaling configuration at its largest size -- unit
 square, h = 2^-11 (2049 x 2049 nodes, 8.4M unknowns y and lambda), y_D =
@@ -10,16 +10,21 @@ iterative refinement.  Inputs are resident in HBM when timing starts; L2 is
 flushed (256 MB write) before every timed step.
 
 Printed JSON line: value = solved unknowns/s over all ranks; fp64_plain = the
-same workload with every operation in FP64; e2e = through mg_solve_host with
-pinned host buffers (copies inside the timed region); roofline = the
-finest-level smoother sweeps (CUDA events inside the solve) against the
-measured HBM copy bandwidth; cpu_baseline = the FP64 CPU oracle on a bounded
-sample.  `--impl reference` times the CPU oracle alone on the same workload.
+same workload with every operation in FP64; e2e = through mg_batch_solve_host
+with pinned host buffers (copies inside the timed region); roofline = the
+finest-level smoother sweep (CUDA events inside a solve) against the measured
+HBM copy bandwidth; roofs_measured = the library's own FMA-rate and bandwidth
+microbenchmarks; l12, batch256, autograd16 = the largest instance, 256 batched
+instances, 16 differentiated instances; stokes = the Stokes control problem at
+h = 2^-9; cpu_baseline = the FP64 CPU oracle on a bounded sample.
+`--impl reference` times the CPU oracle alone on the same workload.
 
 Other modes (not timed against the reference): `--batch N` solves N
 independent instances of mixed size (levels 6..10, alpha log-uniform in
-[1e-8, 1]) at once through mg_solve_batch; `--protocol` prints the iteration
-counts of the paper's section 3 protocol in the layout of its Table 1.
+[1e-8, 1]) in one batch graph; `--protocol` / `--protocol-stokes` print the
+iteration counts of the paper's section 3 protocol in the layout of its
+Table 1 / Table 2; `--profile-band`, `--profile-stokes`,
+`--profile-stokes-step` run small launch sequences for ncu.
 """
 from __future__ import annotations
 
