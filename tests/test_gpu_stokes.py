@@ -147,6 +147,37 @@ def test_protocol_iterations_match_oracle(st, stokes_mod, k, alpha, smoother):
     assert it == ito, (it, ito)
 
 
+@pytest.mark.parametrize("smoother", ["lsgs", "slsgs"])
+def test_protocol_iterations_k6_with_dense_map(st, stokes_mod, smoother):
+    """The protocol at k = 6, where the coarse levels <= 4 run as the dense
+    map: the oracle's count (multicolour order, recursion to h = 1/2)."""
+    k, alpha = 6, 1e-6
+    nu = 1 if smoother == "slsgs" else 2
+    x0 = np.random.default_rng(7).uniform(-1.0, 1.0, inputs.stokes_sizes(k)[2])
+    o = stokes_mod.StokesOracle(k, alpha, smoother=smoother, nu_pre=nu, nu_post=nu)
+    ito = o.protocol_iterations(x0, 1e-6, 300)
+    with st.StokesSolver(k, alpha, smoother=smoother) as s:
+        it = s.protocol_iterations(dev(x0), 1e-6, 300)
+    assert it == ito, (it, ito)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1e-6])
+@pytest.mark.parametrize("L", [4, 6])
+def test_solve_v_cycle(st, stokes_mod, L, alpha):
+    o = stokes_mod.StokesOracle(L, alpha, smoother="lsgs", gamma=1)
+    vD = inputs.stokes_vd_vortex(L, 70 + L)
+    xo, ito, _, _ = o.solve(o.rhs(vD), tol=1e-10, max_iter=200)
+    with st.StokesSolver(L, alpha, smoother="lsgs", cycle="V", max_iter=200) as s:
+        f = s.rhs_from_vd(dev(vD))
+        x = torch.zeros_like(f)
+        it, rr, _ = s.solve(f, x, tol=1e-10)
+        s.normalize(x)
+        xh = host(x)
+    xn = o.normalize(xo)
+    assert it == ito and rr <= 1e-10, (it, ito, rr)
+    assert o.norm_L(xh - xn) <= 1e-9 * o.norm_L(xn)
+
+
 def test_normalize_and_norms(st, stokes_mod):
     L, alpha = 4, 1e-2
     o = stokes_mod.StokesOracle(L, alpha)
