@@ -192,6 +192,47 @@ __device__ __forceinline__ void rows_ne_fast(const LevelP<T>& P, V2* xr, const V
 
 // Algorithm 2 update of one field of the x pair xr[i], with the scatter into
 // the rh rows
+// The field-dependent constants of an interior update: the scatter weights of
+// the centre, edge and diagonal neighbours and N_ii^-1.  A thread whose field
+// is fixed loads them once (a run-time field index would otherwise turn every
+// update's reads of them into indexed constant loads).
+template <typename V2, typename T>
+struct LsgsConsts {
+    V2 cC, cE, cD;
+    T invN;
+};
+
+template <typename T, typename V2>
+__device__ __forceinline__ LsgsConsts<V2, T> lsgs_consts(const LevelP<T>& P, int field) {
+    LsgsConsts<V2, T> c;
+    c.cC = pmake<T>(P.sc[field][0][0], P.sc[field][0][1]);
+    c.cE = pmake<T>(P.sc[field][1][0], P.sc[field][1][1]);
+    c.cD = pmake<T>(P.sc[field][2][0], P.sc[field][2][1]);
+    c.invN = field == 0 ? P.invNy_int : P.invNl_int;
+    return c;
+}
+
+// rows_lsgs_fast with the constants preloaded
+template <typename T, typename V2>
+__device__ __forceinline__ void rows_lsgs_fast_c(const LevelP<T>& P, const LsgsConsts<V2, T>& c, int field, V2* xr,
+                                                 V2* rs, V2* rsp, V2* rsm, int i) {
+    V2 M, K, nb[7];
+    rows_stencil(rs, rsp, rsm, i, psplat(P.mC), psplat(P.mO), M, K, nb);
+    T qy, ql;
+    rows_from_dots(P, M.x, K.x, M.y, K.y, qy, ql);
+    const T pv = (field == 0 ? qy : ql) * c.invN;
+    if (field == 0) xr[i].x += pv;
+    else xr[i].y += pv;
+    const V2 mp = psplat(-pv);
+    rs[i] = pfma(mp, c.cC, nb[0]);
+    rs[i + 1] = pfma(mp, c.cE, nb[1]);
+    rs[i - 1] = pfma(mp, c.cE, nb[2]);
+    rsp[i] = pfma(mp, c.cE, nb[3]);
+    rsm[i] = pfma(mp, c.cE, nb[4]);
+    rsp[i + 1] = pfma(mp, c.cD, nb[5]);
+    rsm[i - 1] = pfma(mp, c.cD, nb[6]);
+}
+
 template <typename T, typename V2>
 __device__ __forceinline__ void rows_lsgs_fast(const LevelP<T>& P, int field, V2* xr, V2* rs, V2* rsp, V2* rsm,
                                                int i) {

@@ -192,10 +192,10 @@ __device__ __forceinline__ void band_resid_fast(const LevelP<T>& P, BandSmem<T, 
     S->R[sr][t] = rows_resid_fast<T>(P, S->X[sx], S->X[sxp], S->X[sxm], t, fv.x, fv.y);
 }
 
-template <typename T, int WT>
-__device__ __forceinline__ void band_update_fast(const LevelP<T>& P, BandSmem<T, WT>* S, int field, int t, int sm,
-                                                 int s, int sp, int sx) {
-    rows_lsgs_fast<T>(P, field, S->X[sx], S->R[s], S->R[sp], S->R[sm], t);
+template <typename T, int WT, typename C>
+__device__ __forceinline__ void band_update_fast(const LevelP<T>& P, const C& c, BandSmem<T, WT>* S, int field,
+                                                 int t, int sm, int s, int sp, int sx) {
+    rows_lsgs_fast_c<T>(P, c, field, S->X[sx], S->R[s], S->R[sp], S->R[sm], t);
 }
 
 // ---------------------------------------------- boundary-column path ----
@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(4 * WT) k_lsgs_band(LevelP<T> P, const T* __re
     // the update roles: field 0 (y, role 1) or 1 (lambda, role 3); the lambda
     // phase that meets a column runs 14 rows below its y phase
     const int field = role == 3 ? 1 : 0;
+    const auto lc = lsgs_consts<T, V2T>(P, field);
     for (int tau = jl; tau <= j1 - 1 + kLag; ++tau) {
         if (role == 0) {
             issue(tau + kPre);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(4 * WT) k_lsgs_band(LevelP<T> P, const T* __re
             if (col_work && j >= jl && j <= jh) {
                 if (j >= jfl && j <= jfh) {
                     if (warp_fast)
-                        band_update_fast<T, WT>(P, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                        band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
                                                 (j + 1) & (kRRing - 1), j & (kRing - 1));
                     else
                         band_update_col<T, WT>(P, C, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
