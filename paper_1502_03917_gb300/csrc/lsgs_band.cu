@@ -101,6 +101,10 @@ __device__ void col_class_init(const LevelP<T>& P, int k, ColClass<T>& C) {
     }
 }
 
+// the block barrier, taken by the task roles from their own loops (each
+// thread passes it once per step)
+__device__ __forceinline__ void block_bar() { asm volatile("bar.sync 0;\n" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -331,43 +335,67 @@ __global__ void __launch_bounds__(4 * WT) k_lsgs_band(LevelP<T> P, const T* __re
     }
     __syncthreads();
 
-    // phase index t* of the y update this column meets at step tau:
-    // t* = 5 (c + 2 tau + 6) mod 7, advancing by 3 (mod 7) per step
-    int ts = (5 * ((((c % 7) + 7) % 7 + 2 * (jl % 7) + 6) % 7)) % 7;
-    // the update roles: field 0 (y, role 1) or 1 (lambda, role 3); the lambda
-    // phase that meets a column runs 14 rows below its y phase
-    const int field = role == 3 ? 1 : 0;
-    const auto lc = lsgs_consts<T, V2T>(P, field);
-    for (int tau = jl; tau <= j1 - 1 + kLag; ++tau) {
-        if (role == 0) {
+    // Each role runs its own loop over the steps; every thread passes the
+    // block barrier once per step.  A role's rows lie in the fast range for
+    // every lane in a warp-uniform interval of steps [ta, tb], where only the
+    // lane's column decides whether it works.
+    const int tau_end = j1 - 1 + kLag;
+    if (role == 0) {
+        const bool out_col = c >= i0 && c < i1;
+        for (int tau = jl; tau <= tau_end; ++tau) {
             issue(tau + kPre);
             // row tau - kLag has all its phases: to the output
             const int ro = tau - kLag;
-            if (ro >= j0 && ro < j1 && c >= i0 && c < i1) {
+            if (out_col && ro >= j0 && ro < j1) {
                 int64_t g = (int64_t)ro * P.ld + c;
                 V2T v = S->X[ro & (kRing - 1)][tid];
                 xout[g] = v.x;
                 xout[g + P.fs] = v.y;
             }
             cp_async_wait<kPre - 1>();  // row tau + 1 has landed
-        } else if (role == 2) {
-            // rh of row rho = tau - 2 from the original iterate
+            block_bar();
+        }
+        cp_async_wait<0>();
+    } else if (role == 2) {
+        // rh of row rho = tau - 2 from the original iterate
+        const int ta = jfl + 2, tb = jfh + 2;
+        for (int tau = jl; tau <= tau_end; ++tau) {
             const int rho = tau - 2;
-            if (col_work && rho >= jl && rho <= jh) {
-                if (rho >= jfl && rho <= jfh) {
+            if (tau >= ta && tau <= tb) {
+                if (col_work) {
                     if (warp_fast)
                         band_resid_fast<T, WT>(P, S, tid, (rho - 1) & (kRing - 1), rho & (kRing - 1),
                                                (rho + 1) & (kRing - 1), rho & (kRRing - 1), rho & (kFRing - 1));
                     else
                         band_resid_col<T, WT>(P, C, S, tid, (rho - 1) & (kRing - 1), rho & (kRing - 1),
                                               (rho + 1) & (kRing - 1), rho & (kRRing - 1), rho & (kFRing - 1));
-                } else
-                    band_resid_general<T, WT>(P, V, c, rho);
+                }
+            } else if (col_work && rho >= jl && rho <= jh) {
+                band_resid_general<T, WT>(P, V, c, rho);
             }
-        } else {
-            // the y phase (role 1) or the lambda phase (role 3) that meets this column now
+            block_bar();
+        }
+    } else {
+        // the y phase (role 1) or the lambda phase (role 3) that meets this
+        // column: phase index t* = 5 (c + 2 tau + 6) mod 7 of the y update,
+        // advancing by 3 (mod 7) per step; the lambda phase runs 14 rows below
+        const int field = role == 3 ? 1 : 0;
+        const auto lc = lsgs_consts<T, V2T>(P, field);
+        int ts = (5 * ((((c % 7) + 7) % 7 + 2 * (jl % 7) + 6) % 7)) % 7;
+        // j = tau - 4 - 2 t* - 14 field lies in [jfl, jfh] for every t* in 0..6
+        const int ta = jfl + 16 + 14 * field, tb = jfh + 4 + 14 * field;
+        for (int tau = jl; tau <= tau_end; ++tau) {
             const int j = tau - 4 - 2 * ts - 14 * field;
-            if (col_work && j >= jl && j <= jh) {
+            if (tau >= ta && tau <= tb) {
+                if (col_work) {
+                    if (warp_fast)
+                        band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                                                (j + 1) & (kRRing - 1), j & (kRing - 1));
+                    else
+                        band_update_col<T, WT>(P, C, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                                               (j + 1) & (kRRing - 1), j & (kRing - 1));
+                }
+            } else if (col_work && j >= jl && j <= jh) {
                 if (j >= jfl && j <= jfh) {
                     if (warp_fast)
                         band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
@@ -379,10 +407,9 @@ __global__ void __launch_bounds__(4 * WT) k_lsgs_band(LevelP<T> P, const T* __re
                     band_update_general<T, WT>(P, V, field, c, j);
             }
             ts = ts >= 4 ? ts - 4 : ts + 3;
+            block_bar();
         }
-        __syncthreads();
     }
-    if (role == 0) cp_async_wait<0>();
 }
 
 }  // namespace
