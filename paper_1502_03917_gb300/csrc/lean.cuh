@@ -190,8 +190,6 @@ __device__ __forceinline__ void rows_ne_fast(const LevelP<T>& P, V2* xr, const V
     xr[i] = v;
 }
 
-// Algorithm 2 update of one field of the x pair xr[i], with the scatter into
-// the rh rows
 // The field-dependent constants of an interior update: the scatter weights of
 // the centre, edge and diagonal neighbours and N_ii^-1.  A thread whose field
 // is fixed loads them once (a run-time field index would otherwise turn every
@@ -233,6 +231,8 @@ __device__ __forceinline__ void rows_lsgs_fast_c(const LevelP<T>& P, const LsgsC
     rsm[i - 1] = pfma(mp, c.cD, nb[6]);
 }
 
+// Algorithm 2 update of one field of the x pair xr[i], with the scatter into
+// the rh rows
 template <typename T, typename V2>
 __device__ __forceinline__ void rows_lsgs_fast(const LevelP<T>& P, int field, V2* xr, V2* rs, V2* rsp, V2* rsm,
                                                int i) {

@@ -101,6 +101,12 @@ __device__ void col_class_init(const LevelP<T>& P, int k, ColClass<T>& C) {
     }
 }
 
+// a field index as a type (the update roles' loops are compiled per field)
+template <int F>
+struct FieldC {
+    static constexpr int value = F;
+};
+
 // the block barrier, taken by the task roles from their own loops (each
 // thread passes it once per step)
 __device__ __forceinline__ void block_bar() { asm volatile("bar.sync 0;\n" ::: "memory"); }
@@ -342,15 +348,26 @@ __global__ void __launch_bounds__(4 * WT) k_lsgs_band(LevelP<T> P, const T* __re
     const int tau_end = j1 - 1 + kLag;
     if (role == 0) {
         const bool out_col = c >= i0 && c < i1;
-        for (int tau = jl; tau <= tau_end; ++tau) {
-            issue(tau + kPre);
+        const int64_t ld = P.ld, fsz = P.fs;
+        int64_t gi = (int64_t)(jl + kPre) * ld;      // element offset of row tau + kPre
+        int64_t go = (int64_t)(jl - kLag) * ld + c;  // element offset of (c, tau - kLag)
+        for (int tau = jl; tau <= tau_end; ++tau, gi += ld, go += ld) {
+            const int row = tau + kPre;
+            if (col_in && row <= jh) {
+                T* xs = reinterpret_cast<T*>(&S->X[row & (kRing - 1)][tid]);
+                T* fs = reinterpret_cast<T*>(&S->F[row & (kFRing - 1)][tid]);
+                cp_async(xs, xin_c + gi);
+                cp_async(xs + 1, xin_c + gi + fsz);
+                cp_async(fs, f_c + gi);
+                cp_async(fs + 1, f_c + gi + fsz);
+            }
+            cp_async_commit();
             // row tau - kLag has all its phases: to the output
             const int ro = tau - kLag;
             if (out_col && ro >= j0 && ro < j1) {
-                int64_t g = (int64_t)ro * P.ld + c;
                 V2T v = S->X[ro & (kRing - 1)][tid];
-                xout[g] = v.x;
-                xout[g + P.fs] = v.y;
+                xout[go] = v.x;
+                xout[go + fsz] = v.y;
             }
             cp_async_wait<kPre - 1>();  // row tau + 1 has landed
             block_bar();
@@ -379,36 +396,40 @@ __global__ void __launch_bounds__(4 * WT) k_lsgs_band(LevelP<T> P, const T* __re
         // the y phase (role 1) or the lambda phase (role 3) that meets this
         // column: phase index t* = 5 (c + 2 tau + 6) mod 7 of the y update,
         // advancing by 3 (mod 7) per step; the lambda phase runs 14 rows below
-        const int field = role == 3 ? 1 : 0;
-        const auto lc = lsgs_consts<T, V2T>(P, field);
-        int ts = (5 * ((((c % 7) + 7) % 7 + 2 * (jl % 7) + 6) % 7)) % 7;
-        // j = tau - 4 - 2 t* - 14 field lies in [jfl, jfh] for every t* in 0..6
-        const int ta = jfl + 16 + 14 * field, tb = jfh + 4 + 14 * field;
-        for (int tau = jl; tau <= tau_end; ++tau) {
-            const int j = tau - 4 - 2 * ts - 14 * field;
-            if (tau >= ta && tau <= tb) {
-                if (col_work) {
-                    if (warp_fast)
-                        band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
-                                                (j + 1) & (kRRing - 1), j & (kRing - 1));
-                    else
-                        band_update_col<T, WT>(P, C, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
-                                               (j + 1) & (kRRing - 1), j & (kRing - 1));
+        auto run = [&](auto fc) {
+            constexpr int field = decltype(fc)::value;
+            const auto lc = lsgs_consts<T, V2T>(P, field);
+            int ts = (5 * ((((c % 7) + 7) % 7 + 2 * (jl % 7) + 6) % 7)) % 7;
+            // j = tau - 4 - 2 t* - 14 field lies in [jfl, jfh] for every t* in 0..6
+            const int ta = jfl + 16 + 14 * field, tb = jfh + 4 + 14 * field;
+            for (int tau = jl; tau <= tau_end; ++tau) {
+                const int j = tau - 4 - 2 * ts - 14 * field;
+                if (tau >= ta && tau <= tb) {
+                    if (col_work) {
+                        if (warp_fast)
+                            band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                                                    (j + 1) & (kRRing - 1), j & (kRing - 1));
+                        else
+                            band_update_col<T, WT>(P, C, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                                                   (j + 1) & (kRRing - 1), j & (kRing - 1));
+                    }
+                } else if (col_work && j >= jl && j <= jh) {
+                    if (j >= jfl && j <= jfh) {
+                        if (warp_fast)
+                            band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                                                    (j + 1) & (kRRing - 1), j & (kRing - 1));
+                        else
+                            band_update_col<T, WT>(P, C, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
+                                                   (j + 1) & (kRRing - 1), j & (kRing - 1));
+                    } else
+                        band_update_general<T, WT>(P, V, field, c, j);
                 }
-            } else if (col_work && j >= jl && j <= jh) {
-                if (j >= jfl && j <= jfh) {
-                    if (warp_fast)
-                        band_update_fast<T, WT>(P, lc, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
-                                                (j + 1) & (kRRing - 1), j & (kRing - 1));
-                    else
-                        band_update_col<T, WT>(P, C, S, field, tid, (j - 1) & (kRRing - 1), j & (kRRing - 1),
-                                               (j + 1) & (kRRing - 1), j & (kRing - 1));
-                } else
-                    band_update_general<T, WT>(P, V, field, c, j);
+                ts = ts >= 4 ? ts - 4 : ts + 3;
+                block_bar();
             }
-            ts = ts >= 4 ? ts - 4 : ts + 3;
-            block_bar();
-        }
+        };
+        if (role == 1) run(FieldC<0>{});
+        else run(FieldC<1>{});
     }
 }
 
