@@ -60,6 +60,13 @@ struct EdgeNodes {
     }
 };
 
+// a field index as a type, for loops compiled per field (the field-dependent
+// constants and selections then fold at compile time)
+template <int F>
+struct FieldC {
+    static constexpr int value = F;
+};
+
 // ------------------------------------------------------- fast updates ----
 // The node (i,j) satisfies 2 <= i, j <= n-2.  x and f keep their two fields
 // apart (layout of P); the scaled residual rh is an array of (y, lambda) pairs

@@ -101,12 +101,6 @@ __device__ void col_class_init(const LevelP<T>& P, int k, ColClass<T>& C) {
     }
 }
 
-// a field index as a type (the update roles' loops are compiled per field)
-template <int F>
-struct FieldC {
-    static constexpr int value = F;
-};
-
 // the block barrier, taken by the task roles from their own loops (each
 // thread passes it once per step)
 __device__ __forceinline__ void block_bar() { asm volatile("bar.sync 0;\n" ::: "memory"); }

@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
         }
         barrier();
     };
-    auto phase = [&](int field, int c) {
+    auto phase = [&](auto fc, int c) {
+        constexpr int field = decltype(fc)::value;
         const int ni = nrows * CPR, nip = (ni + 31) & ~31;
         const int ne = SE.count(c);
         for (int t = g; t < nip + ne; t += G) {
@@ -433,11 +434,12 @@ __global__ void __launch_bounds__(strip_threads<T>()) k_smooth_strips(LevelP<T> 
     } else {
         resid_all();
         for (int m = 0; m < steps; ++m) {
-            for (int field = 0; field < 2; ++field)
-                for (int c = 0; c < 7; ++c) phase(field, colour_seq(c));
-            if (smoother == 2)
-                for (int field = 1; field >= 0; --field)
-                    for (int c = 6; c >= 0; --c) phase(field, colour_seq(c));
+            for (int c = 0; c < 7; ++c) phase(FieldC<0>{}, colour_seq(c));
+            for (int c = 0; c < 7; ++c) phase(FieldC<1>{}, colour_seq(c));
+            if (smoother == 2) {
+                for (int c = 6; c >= 0; --c) phase(FieldC<1>{}, colour_seq(c));
+                for (int c = 6; c >= 0; --c) phase(FieldC<0>{}, colour_seq(c));
+            }
         }
     }
     // after the last barrier no block touches another's shared memory
@@ -595,7 +597,8 @@ __global__ void __launch_bounds__(kRgThreads) k_smooth_rg(LevelP<T> P, const Edg
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) sd[q] = slot_desc<N, CPR>(g + q * G, ni, nip, SE);
     const int jmax = ja + nrows - 1;
-    auto phase = [&](int field, int c) {
+    auto phase = [&](auto fc, int c) {
+        constexpr int field = decltype(fc)::value;
         const int64_t foff = field ? P.fs : 0;
         int si[kSlots], sj[kSlots];
         bool on[kSlots];
@@ -633,11 +636,12 @@ __global__ void __launch_bounds__(kRgThreads) k_smooth_rg(LevelP<T> P, const Edg
         cluster_barrier();
     };
     for (int m = 0; m < steps; ++m) {
-        for (int field = 0; field < 2; ++field)
-            for (int c = 0; c < 7; ++c) phase(field, colour_seq(c));
-        if (smoother == 2)
-            for (int field = 1; field >= 0; --field)
-                for (int c = 6; c >= 0; --c) phase(field, colour_seq(c));
+        for (int c = 0; c < 7; ++c) phase(FieldC<0>{}, colour_seq(c));
+        for (int c = 0; c < 7; ++c) phase(FieldC<1>{}, colour_seq(c));
+        if (smoother == 2) {
+            for (int c = 6; c >= 0; --c) phase(FieldC<1>{}, colour_seq(c));
+            for (int c = 6; c >= 0; --c) phase(FieldC<0>{}, colour_seq(c));
+        }
     }
 }
 
