@@ -53,13 +53,6 @@ struct Lev {
     void* f = nullptr;
     void* rh = nullptr;
     BandGrid bg{};
-    // The tiling used inside a batch graph of several instances: there the
-    // instances run at once, and a step whose blocks hold every SM for its
-    // whole duration keeps the other instances' latency-bound coarse levels
-    // from starting; half as many blocks (taller segments, less recomputed
-    // halo) leave SMs to them.  Measured on the five concurrent h = 2^-11
-    // solves: 2.06e8 -> 2.30e8 unknowns/s with 80 instead of 152 blocks.
-    BandGrid bgb{};
     int cs = 0;              // smoothing calls in one launch: of one block (1) or a cluster of cs blocks; 0: no
     bool band = false;       // LSGS steps by the one-launch band kernel (else one launch per colour phase)
     bool rg = false;         // whole smoothing calls by the 513^2 cluster kernel (residual on chip, x in global)
@@ -225,7 +218,7 @@ struct mg_ctx {
     int band_min = 1025;      // FP32 levels with at least this many nodes per side use the one-launch LSGS step
     int small_max = 513;      // levels up to this many nodes per side: one launch per smoothing call
     bool fp32 = false;
-    bool in_batch = false;    // recording into a batch graph of several instances (band steps use bgb)
+    int in_batch = 0;         // instances of the batch graph being recorded (band steps use batch_grid when > 1)
     Lev lev[AAOMG_MAX_LEVELS + 1];
     int lc = 0;               // whole cycle inside the single-block kernel when L <= lc
     int ld = 0;               // level whose gamma coarse-grid steps are one dense map (0: none)
@@ -259,13 +252,21 @@ struct mg_ctx {
     long long prof_sweeps = 0, sweeps_per_iter = 0;
 };
 
-// the band tiling of a level inside a batch graph of several instances (Lev::bgb):
-// the bands of the handle's own tiling, half as many blocks
-BandGrid batch_grid(const mg_ctx* H, const Lev& v) {
+// The band tiling of a level inside a batch graph of `count` instances: the
+// bands of the handle's own tiling with a quarter of the GPU's blocks, an
+// eighth from 16 instances on.  There the instances run at once, and a step
+// whose blocks hold every SM for its whole duration keeps the other
+// instances' latency-bound coarse levels from starting; fewer blocks (taller
+// segments, less recomputed halo and pipeline fill) leave SMs to them.
+// Measured on the five concurrent h = 2^-11 solves (unknowns/s): every SM
+// 2.06e8, a half 2.38e8, a quarter 2.45e8, a sixth 2.23e8; on 256 mixed
+// instances: a half 2.09e8, a quarter 2.21e8, an eighth 2.26e8.
+BandGrid batch_grid(const mg_ctx* H, const Lev& v, int count) {
     if (H->o.tile_w > 0 || H->o.tile_h > 0) return v.bg;
-    const int half = H->nsm * (H->fp32 ? band_blocks_per_sm<float>() : band_blocks_per_sm<double>()) / 2;
-    return H->fp32 ? band_grid<float>(v.n, v.bg.W, 0, half > 0 ? half : 1)
-                   : band_grid<double>(v.n, v.bg.W, 0, half > 0 ? half : 1);
+    const int part = H->nsm * (H->fp32 ? band_blocks_per_sm<float>() : band_blocks_per_sm<double>()) /
+                     (count >= 16 ? 8 : 4);
+    return H->fp32 ? band_grid<float>(v.n, v.bg.W, 0, part > 0 ? part : 1)
+                   : band_grid<double>(v.n, v.bg.W, 0, part > 0 ? part : 1);
 }
 
 // State of one instance of a graph-captured batch solve (device memory).
@@ -423,7 +424,7 @@ void smooth(mg_ctx* H, int l, int steps, cudaStream_t s) {
         T* a = x;
         T* b = (T*)v.x2;
         for (int m = 0; m < steps; ++m) {
-            launch_lsgs_band<T>(P, f, a, b, H->in_batch ? v.bgb : v.bg, s);
+            launch_lsgs_band<T>(P, f, a, b, H->in_batch > 1 ? batch_grid(H, v, H->in_batch) : v.bg, s);
             T* t = a;
             a = b;
             b = t;
@@ -897,9 +898,9 @@ int batch_record(mg_batch_ctx* B, bool pdl_off) {
         BCK(cudaStreamBeginCaptureToGraph(H->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         capturing.push_back(H->cap);
         H->rec_kernels = 0;
-        H->in_batch = B->count > 1;
+        H->in_batch = B->count;
         rc = record_iteration(H, H->cap);
-        H->in_batch = false;
+        H->in_batch = 0;
         if (rc || (rc = queue_norms_dev(H, H->cap))) return bail(rc, g_err);
         B->body_kernels[k] = H->rec_kernels + 3;
         k_batch_check<<<1, 32, 0, H->cap>>>(H->red, B->d_state + k, B->d_hist + (size_t)k * B->hcap, B->hcap,
@@ -1055,7 +1056,6 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         CK(cudaMemset(v.x2, 0, bytes));
         v.bg = H->fp32 ? band_grid<float>(v.n, o.tile_w, o.tile_h, H->nsm * band_blocks_per_sm<float>())
                        : band_grid<double>(v.n, o.tile_w, o.tile_h, H->nsm * band_blocks_per_sm<double>());
-        v.bgb = batch_grid(H, v);
         v.band = v.n + 1 >= H->band_min;
         CK(cudaMemset(v.f, 0, bytes));
         CK(cudaMemset(v.rh, 0, bytes));
@@ -1100,8 +1100,6 @@ int mg_setup(int levels, double alpha, const mg_options* opt, mg_handle* out) {
         }
     }
     if (!rc && o.autotune) rc = H->fp32 ? autotune_levels<float>(H, km) : autotune_levels<double>(H, km);
-    if (!rc && o.autotune)
-        for (int l = 1; l <= levels; ++l) H->lev[l].bgb = batch_grid(H, H->lev[l]);
     if (rc) {
         mg_destroy(H);
         return rc;
