@@ -413,9 +413,10 @@ def test_level_513_cluster_kernel(mg, oracle_mod, smoother, alpha):
 def test_profile_of_one_level(mg):
     """profile_level times the smoothing calls of that level: a W-cycle from
     level 8 visits level 6 four times, with nu_pre + nu_post = 4 steps a visit,
-    in each of the inner cycles of every refinement step."""
+    in each of the 3 inner cycles of every refinement step."""
     L = 8
-    with mg.Solver(L, 1e-2, smoother="lsgs", precision="fp32_refine", profile=True, profile_level=6) as s:
+    with mg.Solver(L, 1e-2, smoother="lsgs", precision="fp32_refine", profile=True, profile_level=6,
+                   inner_cycles=3) as s:
         f = s.rhs_from_yd(dev(inputs.yd_sine_noise(L, 1)))
         x = torch.zeros_like(f)
         it, rr, code = s.solve(f, x, tol=1e-6)
